@@ -1,0 +1,150 @@
+/*
+ * CPU ORACLE -- test infrastructure only.
+ *
+ * A plain, serial, obviously correct statement of what the BFS library computes.
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg use it;
+ * the library itself never calls, links or loads anything from this directory.
+ * It shares no code with the CUDA path.
+ *
+ * What it computes (the plain definitions the paper's method reaches exactly):
+ *   - graph: the undirected graph of an edge list, stored as CSR with each
+ *     undirected edge stored in both rows, rows sorted ascending, self-loops
+ *     and repeated pairs dropped (Sec. 4.1 "Graph Representation"; the
+ *     benchmark symmetrises its input, Sec. 6).
+ *   - level[v] = d(s, v), the hop distance from s (Sec. 2.1, Algorithm 1), or -1
+ *     when v is unreachable (the int32 stand-in for Algorithm 1's infinity).
+ *   - parent[s] = s; for reached v != s, parent[v] = the largest id u adjacent to
+ *     v with level[u] = level[v] - 1.  This is the (select2nd, max) semiring
+ *     product of Sec. 3.2 / Algorithm 3 with frontier values equal to the
+ *     vertices' own ids; parent[v] = -1 when v is unreachable (Algorithm 3's
+ *     output contract).
+ *   - TEPS edge count of a traversal: the undirected edges inside the reached
+ *     component, half the degree sum of the reached vertices (Sec. 6).
+ *
+ * Algorithm: the queue-based serial BFS the paper contrasts with its two-stack
+ * Algorithm 1 (Sec. 2.1 -- both give the same levels), followed by a separate
+ * pass that applies the max-id parent definition vertex by vertex.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+static int oracle_cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/*
+ * Builds the symmetric CSR of an edge list.
+ *   offsets: int64[n+1] (written), adj: int32 scratch of capacity 2*m; on return
+ *   its first nnz entries hold the rows.  Returns nnz, or -1 on a bad argument
+ *   (an endpoint outside [0, n)).
+ * Steps: count both directions of every non-loop edge per row, prefix-sum the
+ * counts into row starts, scatter, sort every row, drop repeats within each row
+ * and pack the rows to the front.
+ */
+int64_t oracle_build_csr(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
+                         int64_t* offsets, int32_t* adj) {
+  if (n < 0 || m < 0 || !offsets || (m > 0 && (!src || !dst || !adj))) return -1;
+  for (int64_t e = 0; e < m; ++e)
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return -1;
+
+  int64_t* fill = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!fill) return -1;
+  for (int64_t i = 0; i <= n; ++i) offsets[i] = 0;
+  for (int64_t e = 0; e < m; ++e) {
+    if (src[e] == dst[e]) continue;
+    offsets[src[e] + 1] += 1;
+    offsets[dst[e] + 1] += 1;
+  }
+  for (int64_t v = 0; v < n; ++v) offsets[v + 1] += offsets[v];
+  for (int64_t v = 0; v < n; ++v) fill[v] = offsets[v];
+  for (int64_t e = 0; e < m; ++e) {
+    int32_t u = src[e], v = dst[e];
+    if (u == v) continue;
+    adj[fill[u]++] = v;
+    adj[fill[v]++] = u;
+  }
+  /* sort each row and drop repeats; rows are packed towards the front */
+  int64_t out = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t b = offsets[v], e = offsets[v + 1];
+    qsort(adj + b, (size_t)(e - b), sizeof(int32_t), oracle_cmp_i32);
+    int64_t row_start = out;
+    for (int64_t i = b; i < e; ++i) {
+      if (i > b && adj[i] == adj[i - 1]) continue;
+      adj[out++] = adj[i];
+    }
+    offsets[v] = row_start;
+  }
+  offsets[n] = out;
+  free(fill);
+  return out;
+}
+
+/*
+ * Serial BFS from s.  level, parent: int32[n] (written); queue: int32[n] scratch.
+ * Returns the number of levels (1 + the largest finite level), or -1 on a bad
+ * argument.
+ */
+int32_t oracle_bfs(const int64_t* offsets, const int32_t* adj, int32_t n, int32_t s,
+                   int32_t* level, int32_t* parent, int32_t* queue) {
+  if (n <= 0 || s < 0 || s >= n || !offsets || !level || !parent || !queue) return -1;
+  for (int32_t v = 0; v < n; ++v) {
+    level[v] = -1;
+    parent[v] = -1;
+  }
+  /* levels: FIFO queue, each vertex gets level[u] + 1 the first time it is seen */
+  int64_t head = 0, tail = 0;
+  level[s] = 0;
+  queue[tail++] = s;
+  int32_t deepest = 0;
+  while (head < tail) {
+    int32_t u = queue[head++];
+    for (int64_t i = offsets[u]; i < offsets[u + 1]; ++i) {
+      int32_t v = adj[i];
+      if (level[v] == -1) {
+        level[v] = level[u] + 1;
+        if (level[v] > deepest) deepest = level[v];
+        queue[tail++] = v;
+      }
+    }
+  }
+  /* parents: the largest neighbour one level closer to s */
+  parent[s] = s;
+  for (int32_t v = 0; v < n; ++v) {
+    if (level[v] <= 0) continue;
+    int32_t best = -1;
+    for (int64_t i = offsets[v]; i < offsets[v + 1]; ++i) {
+      int32_t u = adj[i];
+      if (level[u] == level[v] - 1 && u > best) best = u;
+    }
+    parent[v] = best;
+  }
+  return deepest + 1;
+}
+
+/* Undirected edges inside the reached set: half the degree sum of reached vertices. */
+int64_t oracle_component_edges(const int64_t* offsets, const int32_t* level, int32_t n) {
+  int64_t sum = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (level[v] >= 0) sum += offsets[v + 1] - offsets[v];
+  return sum / 2;
+}
+
+/*
+ * Per-level frontier statistics of a finished traversal: for k < nlevels,
+ * count[k] = |{v : level[v] = k}| and edges[k] = sum of their degrees.
+ */
+int oracle_level_stats(const int64_t* offsets, const int32_t* level, int32_t n, int32_t nlevels,
+                       int64_t* count, int64_t* edges) {
+  if (nlevels < 0 || !count || !edges) return -1;
+  for (int32_t k = 0; k < nlevels; ++k) count[k] = edges[k] = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    int32_t k = level[v];
+    if (k < 0 || k >= nlevels) continue;
+    count[k] += 1;
+    edges[k] += offsets[v + 1] - offsets[v];
+  }
+  return 0;
+}
