@@ -1,0 +1,279 @@
+/*
+ * bfs.h -- C ABI of the GB300 breadth-first search library (libbfs_gb300.so).
+ *
+ * The library computes level-synchronous BFS on an undirected, unweighted graph
+ * G = (V, E) (Sec. 2.1 of Buluc & Madduri, "Parallel Breadth-First Search on
+ * Distributed Memory Systems").  Each level is one sparse matrix-sparse vector
+ * product over the (select2nd, max) semiring, masked by the vertices already
+ * reached (Sec. 3.2, Algorithm 3): with frontier values equal to the vertices'
+ * own ids, a newly reached vertex takes as parent its LARGEST-id neighbour in
+ * the previous frontier, which makes the BFS tree unique.
+ *
+ * Outputs of every traversal, for a source s:
+ *   level[v]  = d(s, v), the hop distance (Algorithm 1's d), or -1 if v is not
+ *               reachable from s;
+ *   parent[v] = s for v = s; the largest-id neighbour u of v with
+ *               level[u] = level[v] - 1 otherwise; -1 if v is not reachable
+ *               (Algorithm 3's output pi).
+ *
+ * Conventions for every entry point:
+ *   - Vertex ids are int32 in [0, n); CSR row offsets are int64 (the directed
+ *     entry count of a large graph exceeds 2^31).
+ *   - Pointers are DEVICE pointers (cudaMalloc or torch CUDA memory on the
+ *     current device) unless a BFS_HOST_PTRS flag says otherwise.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued asynchronously on it; results are valid once the stream
+ *     has reached the work (synchronise it, or call bfs_sync).
+ *   - Every call returns a bfs_status; on failure bfs_last_error() gives a
+ *     message (thread-local, valid until the next call on the same thread).
+ *   - A graph is immutable after creation.  Runs on one graph from different
+ *     host threads must use different streams; each stream gets its own
+ *     workspace, created on first use and kept until bfs_graph_destroy.
+ */
+#ifndef BFS_GB300_H
+#define BFS_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BFS_API __attribute__((visibility("default")))
+#else
+#define BFS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bfs_status {
+  BFS_OK = 0,
+  BFS_ERR_INVALID_ARG = 1,   /* bad source, NULL pointer, size out of range */
+  BFS_ERR_INVALID_GRAPH = 2, /* BFS_VALIDATE found a malformed CSR */
+  BFS_ERR_OOM = 3,           /* a device allocation failed */
+  BFS_ERR_CUDA = 4,          /* a CUDA runtime call failed (message has the CUDA error) */
+  BFS_ERR_TIMEOUT = 5,       /* a device-side wait hit its iteration limit; the run was abandoned */
+  BFS_ERR_UNSUPPORTED = 6    /* no CUDA device, or a device older than sm_103 */
+} bfs_status;
+
+/* Flags of bfs_graph_create / bfs_graph_create_from_edges / bfs_opts.flags. */
+#define BFS_HOST_PTRS 0x1u /* the input (graph create) or output (run) pointers are host memory */
+#define BFS_VALIDATE 0x2u  /* graph create: check the CSR on the device before accepting it */
+
+/* Per-level expansion variants (each gives identical levels and parents). */
+typedef enum bfs_variant {
+  BFS_VARIANT_TD_THREAD = 0, /* top-down SpMSV, one thread per frontier vertex */
+  BFS_VARIANT_TD_WARP = 1,   /* top-down SpMSV, one warp per frontier vertex */
+  BFS_VARIANT_TD_BINNED = 2, /* top-down SpMSV, thread / warp / CTA per vertex by degree bin */
+  BFS_VARIANT_PULL = 3,      /* dense-frontier SpMV: unvisited rows scan their adjacency, largest id first */
+  BFS_NUM_VARIANTS = 4
+} bfs_variant;
+
+/* How bfs_run picks the variant of each level. */
+typedef enum bfs_selector {
+  BFS_SELECT_HEURISTIC = 0, /* fixed thresholds on frontier / unvisited edge counts */
+  BFS_SELECT_LEARNED = 1,   /* the selector network set by bfs_selector_set_params (heuristic if none) */
+  BFS_SELECT_FORCED = 2,    /* opts.forced_variant at every level */
+  BFS_SELECT_SCHEDULE = 3   /* opts.schedule[k] at level k (the heuristic beyond schedule_len) */
+} bfs_selector;
+
+/* Statistics of one level k of a traversal (filled when bfs_opts.stats != NULL). */
+typedef struct bfs_level_stat {
+  int64_t frontier_count;   /* |f_k| */
+  int64_t frontier_edges;   /* sum of the degrees of f_k */
+  int64_t bin_count[3];     /* vertices of f_k with degree <= 32, <= 1024, larger */
+  int64_t unvisited_count;  /* vertices not reached before level k+1 starts: n - sum_{i<=k} |f_i| */
+  int64_t unvisited_edges;  /* nnz - sum_{i<=k} sum deg f_i */
+  int64_t time_ns;          /* device time of level k (global timer, between grid barriers) */
+  int32_t variant;          /* bfs_variant used to expand level k */
+  int32_t reserved;
+} bfs_level_stat;
+
+/* Tuning knobs (bfs_autotune fills them; zero fields mean "library default"). */
+typedef struct bfs_tuning {
+  int32_t warp_degree;   /* TD_BINNED: degree from which a vertex gets a warp (default 32) */
+  int32_t cta_degree;    /* TD_BINNED: degree from which a vertex gets a CTA (default 1024) */
+  int32_t pull_thread_degree; /* PULL: rows up to this degree are scanned by one thread (default 32) */
+  int32_t chunk_degree;  /* top-down: vertices above this degree are split into grid-wide chunks (default 16384) */
+  float alpha;           /* heuristic: go PULL when frontier edges > unvisited edges / alpha (default 14) */
+  float beta;            /* heuristic: leave PULL when frontier count < n / beta (default 24) */
+  int32_t batch_topdown_limit; /* batched: levels with at most this many active vertices expand top-down (default n/64) */
+  int32_t reserved;
+} bfs_tuning;
+
+/* Options of one run (NULL = heuristic selector, no statistics). */
+typedef struct bfs_opts {
+  int32_t selector;          /* bfs_selector */
+  int32_t forced_variant;    /* BFS_SELECT_FORCED */
+  const int32_t* schedule;   /* BFS_SELECT_SCHEDULE: host array of schedule_len variants */
+  int32_t schedule_len;
+  int32_t max_stat_levels;   /* capacity of `stats` (levels beyond it are not recorded) */
+  bfs_level_stat* stats;     /* host array; when set, the call synchronises the stream */
+  int32_t* nlevels_out;      /* host int; when set, the call synchronises and writes the level count */
+  int64_t* edges_out;        /* host int64; when set, the call synchronises and writes the TEPS edge
+                                count of the traversal (undirected edges inside the reached set) */
+  uint32_t spin_limit;       /* device wait limit in polls (0 = default, about one second) */
+  uint32_t flags;            /* BFS_HOST_PTRS: parent_out/level_out are host memory */
+} bfs_opts;
+
+typedef struct bfs_graph bfs_graph;
+
+/*
+ * Graph from a CSR of an undirected graph (Sec. 4.1: rows sorted, each edge
+ * stored in both rows).  offsets: int64[n+1], adj: int32[nnz], nnz = offsets[n].
+ * The library copies both arrays into memory it owns; the caller keeps its
+ * inputs.  With BFS_VALIDATE the copy is checked on the device (offsets
+ * monotone from 0 to nnz, ids in range, rows strictly ascending, no
+ * self-loops, symmetric) and BFS_ERR_INVALID_GRAPH is returned if it fails.
+ * Without it a malformed CSR gives unspecified (but memory-safe for in-range
+ * ids) results.  Requires 1 <= n < 2^31 - 1 and 0 <= nnz < 2^40.
+ */
+BFS_API int bfs_graph_create(const int64_t* offsets, const int32_t* adj, int32_t n, int64_t nnz,
+                     uint32_t flags, bfs_graph** out);
+
+/*
+ * Graph from an undirected edge list src/dst: int32[m] (device memory, or host
+ * with BFS_HOST_PTRS).  Built on the device: self-loops dropped, both
+ * directions emitted, 64-bit keys (u, v) radix-sorted, repeats removed, int64
+ * row offsets from the sorted keys (the symmetrised, deduplicated input of the
+ * paper's benchmark, Sec. 6).  Endpoints outside [0, n) give
+ * BFS_ERR_INVALID_ARG.  Temporary device memory of about 40 bytes per edge is
+ * allocated and released inside the call, which synchronises `stream`.
+ */
+BFS_API int bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
+                                uint32_t flags, void* stream, bfs_graph** out);
+
+/*
+ * Block-diagonal union of `count` graphs (vertex ids of part i shifted by the
+ * sum of the sizes of parts 0..i-1).  The union owns a copy; the parts may be
+ * destroyed afterwards.  Used by bfs_run_ragged.  Synchronises `stream`.
+ */
+BFS_API int bfs_graph_union(bfs_graph* const* graphs, int32_t count, void* stream, bfs_graph** out);
+
+/* n, nnz (directed CSR entries) and, for a union, the number of parts (1 otherwise). */
+BFS_API int bfs_graph_info(const bfs_graph* g, int32_t* n, int64_t* nnz, int32_t* parts);
+
+/* Device pointers of the graph's own CSR (read-only for the caller). */
+BFS_API int bfs_graph_csr(const bfs_graph* g, const int64_t** offsets, const int32_t** adj);
+
+/* Copies the graph's CSR into caller buffers offsets_out int64[n+1] and
+ * adj_out int32[nnz] (device memory, or host with BFS_HOST_PTRS).  Synchronous. */
+BFS_API int bfs_graph_copy_csr(const bfs_graph* g, int64_t* offsets_out, int32_t* adj_out, uint32_t flags);
+
+/* Frees the graph and every workspace created for it.  Synchronises the device. */
+BFS_API void bfs_graph_destroy(bfs_graph* g);
+
+/*
+ * One BFS from `source` (Algorithm 3 on one GPU): writes level_out and
+ * parent_out, int32[n] each, caller-allocated.  Runs as ONE persistent
+ * cooperative kernel launch per traversal: every level is an expansion phase
+ * followed by a grid-wide barrier, with the level count held on the device.
+ * Asynchronous unless opts asks for statistics or host outputs.  Device-side
+ * failures (BFS_ERR_TIMEOUT) are returned by bfs_sync or by a synchronising
+ * call; until then further runs on the same stream do no work.
+ */
+BFS_API int bfs_run(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_out,
+            const bfs_opts* opts, void* stream);
+
+/*
+ * BFS from k sources at once: outputs are root-major int32[k][n] (row i belongs
+ * to sources[i], a host array).  Up to 64 roots share one traversal in which
+ * every vertex carries 64-bit frontier and visited bitsets (a boolean sparse
+ * matrix-dense matrix product per level); parents follow the same max-id rule,
+ * recovered by scanning each newly reached vertex's row from the largest id
+ * down.  k > 64 runs in chunks of 64.  Results equal k calls of bfs_run.
+ * Only the heuristic choice between top-down and pull per level applies.
+ */
+BFS_API int bfs_run_batch(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* parent_out,
+                  int32_t* level_out, const bfs_opts* opts, void* stream);
+
+/*
+ * One traversal per part of a union graph (bfs_graph_union), all in one
+ * launch: sources[i] (host array, a LOCAL id of part i) seeds part i.  Because
+ * the parts are disjoint and the id shift keeps the order of ids inside a part,
+ * a single multi-source BFS of the union gives every part exactly its own
+ * levels and max-id parents.  parent_out[i] / level_out[i] are device arrays of
+ * part i's size and receive LOCAL ids.  parent_out and level_out are host
+ * arrays of `parts` device pointers.
+ */
+BFS_API int bfs_run_ragged(bfs_graph* u, const int32_t* sources, int32_t* const* parent_out,
+                   int32_t* const* level_out, const bfs_opts* opts, void* stream);
+
+/* Waits for the stream and returns (and clears) the device status of the last
+ * run enqueued on it for graph g. */
+BFS_API int bfs_sync(bfs_graph* g, void* stream);
+
+/* Tuning of a graph (copied in / out). */
+BFS_API int bfs_set_tuning(bfs_graph* g, const bfs_tuning* t);
+BFS_API int bfs_get_tuning(const bfs_graph* g, bfs_tuning* t);
+
+/*
+ * Times bfs_run over `nroots` host roots (ids) for a small grid of tuning
+ * candidates (bin degrees, pull thread degree, chunk degree, heuristic alpha and
+ * beta), keeps the fastest as the graph's tuning and copies it to *best.
+ * Synchronises the stream; results never change, only speed.
+ */
+BFS_API int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning* best, void* stream);
+
+/* ---------------- the per-level variant selector network ---------------- */
+/*
+ * Network 12 -> 64 -> 64 -> 4, ReLU, float32, parameters packed flat as
+ * W1[12][64], b1[64], W2[64][64], b2[64], W3[64][4], b3[4] (5,252 floats).
+ * Inputs are the level features listed with bfs_level_features; outputs are
+ * predicted log2 level times in microseconds of the four variants, and the
+ * selector takes the argmin.  (The paper's counterpart is its choice between
+ * two SpMSV accumulators by concurrency, Sec. 4.2.)
+ */
+#define BFS_MLP_PARAMS 5252
+#define BFS_MLP_IN 12
+#define BFS_MLP_OUT 4
+
+/* Forward pass: X float[B][12], Y float[B][4] (device). */
+BFS_API int bfs_mlp_forward(const float* params, const float* X, int32_t B, float* Y, void* stream);
+
+/* Mean squared error over B x 4 against T float[B][4] and its gradient
+ * grad float[5252]; loss float[1] (all device).  Deterministic (fixed
+ * reduction order). */
+BFS_API int bfs_mlp_loss_grad(const float* params, const float* X, const float* T, int32_t B, float* grad,
+                      float* loss, void* stream);
+
+/* One Adam step (bias-corrected, step t >= 1) on params, with moments m, v (device). */
+BFS_API int bfs_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t t, float lr,
+                 float beta1, float beta2, float eps, void* stream);
+
+/* Full-batch Adam training for `steps` steps on device data; params updated in
+ * place; loss_history (device float[steps]) may be NULL. */
+BFS_API int bfs_selector_train(float* params, const float* X, const float* T, int32_t B, int32_t steps,
+                       float lr, float* loss_history, void* stream);
+
+/* Sets (params != NULL, host float[5252]) or clears (NULL) the network used by
+ * BFS_SELECT_LEARNED in this process. */
+BFS_API int bfs_selector_set_params(const float* params);
+
+/* Loads / saves the network as a raw little-endian float32[5252] file. */
+BFS_API int bfs_selector_load(const char* path);
+BFS_API int bfs_selector_save(const char* path);
+
+/*
+ * The 12 selector inputs of a level, from integer level statistics (host):
+ * log2 n / 32, log2 nnz / 32, log2(1 + k) / 10, log2(1 + |f|) / 32,
+ * log2(1 + sum deg f) / 32, |f| / n, sum deg f / nnz, unvisited / n,
+ * unvisited edges / nnz, and the fraction of f with degree <= 32, <= 1024 and
+ * larger.  "Unvisited" means not in levels 0..k, exactly the
+ * unvisited_count / unvisited_edges fields of bfs_level_stat.  The device
+ * computes the same expressions in float32 inside bfs_run.
+ */
+BFS_API int bfs_level_features(int32_t n, int64_t nnz, int32_t k, int64_t frontier_count,
+                       int64_t frontier_edges, int64_t unvisited_count, int64_t unvisited_edges,
+                       const int64_t* bin_count, float* out12);
+
+/* Message of the last failed call on this thread ("" if none). */
+BFS_API const char* bfs_last_error(void);
+
+/* Library version string. */
+BFS_API const char* bfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFS_GB300_H */

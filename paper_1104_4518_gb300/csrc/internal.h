@@ -1,0 +1,163 @@
+// Host-side internals of libbfs_gb300 shared by its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bfs.h"
+
+namespace bfsint {
+
+// ---------------- error reporting ----------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define BFS_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return bfsint::cuda_fail(_e, #expr); \
+  } while (0)
+
+// Device allocation that reports OOM as BFS_ERR_OOM.
+int dev_alloc(void** p, size_t bytes, const char* what);
+
+// ---------------- device properties ----------------
+struct DeviceInfo {
+  int device = -1;
+  int sm_count = 0;
+  int major = 0, minor = 0;
+};
+int current_device_info(DeviceInfo* out);
+
+// ---------------- level counters (device) ----------------
+// One slot per level in a ring of kCtrRing: filled while the frontier of that
+// level is built, read after the grid barrier that ends the phase.
+constexpr int kCtrRing = 8;
+struct __align__(64) LevelCtr {
+  unsigned int count;             // frontier vertices (also the queue tail)
+  unsigned int chunks;            // chunk items of high-degree frontier vertices
+  unsigned long long edges;       // degree sum of the frontier
+  unsigned long long bins[3];     // degree <= 32, <= 1024, larger
+  unsigned long long pad;
+};
+
+// Edges per chunk item of a high-degree top-down vertex (one CTA pass).
+constexpr int kChunkEdges = 4096;
+
+// Device stats record written by the level loop (mirrors bfs_level_stat).
+static_assert(sizeof(bfs_level_stat) == 72, "bfs_level_stat layout");
+
+// ---------------- workspace of single / multi-source runs ----------------
+struct Workspace {
+  cudaStream_t stream = nullptr;
+  int32_t n = 0;
+  int32_t nwords = 0;
+  int32_t* queue[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint32_t* bits[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint32_t* vis = nullptr;
+  int64_t* chunks[2] = {nullptr, nullptr};
+  int64_t chunk_cap = 0;
+  LevelCtr* ctr = nullptr;
+  void* barrier = nullptr;  // bfsdev::GridBarrier
+  int* status = nullptr;
+  bfs_level_stat* stats = nullptr;  // device, kMaxStatLevels
+  int32_t* misc = nullptr;          // [0] level count, [1..] spare
+  long long* edges_out = nullptr;   // device TEPS edge count
+  int32_t* schedule = nullptr;      // device, kMaxSchedule
+  int32_t* sources = nullptr;       // device, up to kMaxSources
+  int32_t* tmp_level = nullptr;     // union-space outputs (ragged / host outputs), lazily
+  int32_t* tmp_parent = nullptr;
+  // batched (64-root bitset) state, lazily
+  uint64_t* bset[3] = {nullptr, nullptr, nullptr};
+  uint64_t* bvis = nullptr;
+  // pinned host staging for schedules and multi-source seeds; `stage_ev` is
+  // recorded after each copy out of it and waited on before it is rewritten
+  int32_t* h_stage = nullptr;
+  cudaEvent_t stage_ev = nullptr;
+  // ragged output pointer tables
+  int32_t** part_out = nullptr;
+  // scratch for bfs_graph_union / misc
+};
+
+constexpr int kMaxStatLevels = 8192;
+constexpr int kMaxSchedule = 8192;
+constexpr int kMaxSources = 4096;
+
+}  // namespace bfsint
+
+struct bfs_graph {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int64_t* d_off = nullptr;
+  int32_t* d_adj = nullptr;
+  int32_t parts = 1;
+  std::vector<int64_t> part_base;  // parts + 1 entries (union graphs)
+  int64_t* d_part_base = nullptr;
+  bfs_tuning tuning{};
+  int device = 0;
+  std::mutex mu;
+  std::vector<bfsint::Workspace*> ws;
+};
+
+namespace bfsint {
+
+// Waits until the pinned staging buffer of w may be rewritten.
+int stage_wait(Workspace* w);
+// Workspace of (g, stream), created on first use.
+int get_workspace(bfs_graph* g, cudaStream_t s, Workspace** out);
+void free_workspace(Workspace* w);
+int ensure_batch_state(bfs_graph* g, Workspace* w);
+int ensure_tmp_outputs(bfs_graph* g, Workspace* w);
+
+// Effective tuning with defaults filled in.
+bfs_tuning effective_tuning(const bfs_graph* g);
+
+// ---------------- kernels (launchers) ----------------
+// CSR construction from an edge list (device pointers).  Allocates d_off/d_adj.
+int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n,
+                         cudaStream_t s, int64_t** d_off, int32_t** d_adj, int64_t* nnz);
+// Adds off_shift to n_part offsets and id_shift to nnz_part ids (union building).
+int union_shift(int64_t* off, int32_t* adj, int64_t n_part, int64_t nnz_part, int64_t off_shift, int32_t id_shift,
+                cudaStream_t s);
+// CSR validation on the device; *ok = 1 when valid.
+int validate_csr(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64_t nnz, cudaStream_t s, int* ok);
+
+struct RunRequest {
+  bfs_graph* g = nullptr;
+  Workspace* w = nullptr;
+  const int32_t* h_sources = nullptr;  // host, union ids
+  int32_t nsources = 0;
+  int32_t* level = nullptr;   // device outputs (union space)
+  int32_t* parent = nullptr;
+  int32_t selector = BFS_SELECT_HEURISTIC;
+  int32_t forced = 0;
+  const int32_t* h_schedule = nullptr;
+  int32_t schedule_len = 0;
+  bool want_stats = false;
+  unsigned spin_limit = 0;
+  // ragged: scatter union outputs into per-part outputs (device table of 2*parts pointers)
+  int32_t** part_out = nullptr;
+};
+int launch_level_loop(const RunRequest& r, cudaStream_t s);
+
+struct BatchRequest {
+  bfs_graph* g = nullptr;
+  Workspace* w = nullptr;
+  const int32_t* h_sources = nullptr;  // up to 64
+  int32_t k = 0;
+  int32_t* level = nullptr;   // device [k][n]
+  int32_t* parent = nullptr;
+  unsigned spin_limit = 0;
+  bool want_stats = false;
+};
+int launch_batch(const BatchRequest& r, cudaStream_t s);
+
+// Selector network parameters on the current device (nullptr if none).
+const float* learned_params_device();
+
+}  // namespace bfsint

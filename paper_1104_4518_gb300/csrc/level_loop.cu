@@ -1,0 +1,652 @@
+// Level-synchronous BFS as one persistent cooperative kernel per traversal.
+//
+// Each level k is one sparse matrix-sparse vector product over the
+// (select2nd, max) semiring followed by the mask with the visited set, the
+// parent update and the frontier replacement (Sec. 3.2, Algorithm 3 on one
+// device).  A level is one phase of the kernel; phases are separated by a
+// grid-wide barrier, and the loop's control (frontier size, variant choice,
+// termination) lives on the device, so a whole traversal is a single launch.
+//
+// State of a phase k (all in HBM, the bitmaps stay resident in L2):
+//   cur  = bits[k % 3]        frontier f_k as a bitmap (read only)
+//   nxt  = bits[(k + 1) % 3]  f_{k+1} being built (claims by atomicOr / owner stores)
+//   clr  = bits[(k + 2) % 3]  f_{k-1}, cleared during the phase for reuse as nxt
+//   vis  = visited bitmap; during phase k it holds levels <= k-1 (and possibly k),
+//          so "reached" is tested as (vis | cur)
+//   queue[k % 3]              f_k as a list; queue[(k + 1) % 3] receives f_{k+1}
+//   ctr[k % 8]                counters of f_k (size, degree sum, degree bins)
+//
+// Variants (identical results):
+//   top-down (thread / warp / degree-binned): for u in f_k and every neighbour w
+//     not yet reached, atomicMax(parent[w], u) -- every frontier neighbour of w
+//     contributes, so parent[w] ends as the largest-id one -- and the first
+//     atomicOr on nxt claims w (level, queue, counters).  Vertices above the
+//     chunk degree are split into grid-wide chunk items of kChunkEdges edges.
+//   pull: for every vertex v not yet reached, scan its sorted row from the
+//     largest id down; the first neighbour in f_k is the max-id parent.  One
+//     warp owns 32 consecutive vertices (one bitmap word), so nxt / vis words
+//     are written without atomics and the next queue is compacted by ballot.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "internal.h"
+#include "mlp_device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace bfsint {
+namespace {
+
+using bfsdev::kFull;
+
+constexpr int kBlock = 512;
+constexpr int kWarps = kBlock / 32;
+
+struct LoopParams {
+  const int64_t* __restrict__ off;
+  const int32_t* __restrict__ adj;
+  int32_t n;
+  int32_t nwords;
+  long long nnz;
+  int32_t* level;
+  int32_t* parent;
+  int32_t* queue[3];
+  uint32_t* bits[3];
+  uint32_t* vis;
+  int64_t* chunks[2];
+  LevelCtr* ctr;
+  bfsdev::GridBarrier* bar;
+  int* status;
+  bfs_level_stat* stats;
+  int32_t* misc;
+  long long* edges_out;
+  const int32_t* sources;  // device list when nsources > 1
+  int32_t src0;            // the source when nsources == 1
+  int32_t nsources;
+  int32_t selector;
+  int32_t forced;
+  const int32_t* schedule;
+  int32_t schedule_len;
+  const float* mlp;
+  int32_t want_stats;
+  unsigned spin_limit;
+  int32_t warp_deg, cta_deg, pull_thread_deg, chunk_deg;
+  float alpha, beta;
+  int32_t parts;
+  const int64_t* part_base;
+  int32_t** part_out;  // [2 * parts]: level outputs then parent outputs
+};
+
+// Per-thread accumulation of the next frontier's counters.
+struct Acc {
+  unsigned long long edges = 0, b0 = 0, b1 = 0, b2 = 0;
+};
+
+__device__ __forceinline__ void acc_vertex(Acc& a, long long deg) {
+  a.edges += (unsigned long long)deg;
+  if (deg <= 32) a.b0 += 1;
+  else if (deg <= 1024) a.b1 += 1;
+  else a.b2 += 1;
+}
+
+// Appends the chunk items of a high-degree vertex of level knext.
+__device__ __forceinline__ void push_chunks(const LoopParams& p, int knext, int v, long long deg) {
+  const unsigned nch = (unsigned)((deg + kChunkEdges - 1) / kChunkEdges);
+  const unsigned pos = atomicAdd(&p.ctr[knext % kCtrRing].chunks, nch);
+  int64_t* dst = p.chunks[knext & 1];
+  for (unsigned c = 0; c < nch; ++c) dst[pos + c] = ((int64_t)v << 32) | (int64_t)c;
+}
+
+// Bookkeeping of a vertex claimed for level knext (the caller already set nxt).
+__device__ __forceinline__ void claim_topdown(const LoopParams& p, int knext, int w, Acc& acc) {
+  p.level[w] = knext;
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)g.size());
+  base = g.shfl(base, 0);
+  p.queue[knext % 3][base + g.thread_rank()] = w;
+  const long long deg = __ldg(&p.off[w + 1]) - __ldg(&p.off[w]);
+  acc_vertex(acc, deg);
+  if (deg > p.chunk_deg) push_chunks(p, knext, w, deg);
+}
+
+// Top-down visit of edge (u -> w) in phase k.
+__device__ __forceinline__ void td_visit(const LoopParams& p, const uint32_t* cur, uint32_t* nxt, int k,
+                                         int u, int w, Acc& acc) {
+  const int ww = w >> 5;
+  const uint32_t m = 1u << (w & 31);
+  const uint32_t seen = p.vis[ww] | cur[ww];
+  if (seen & m) return;
+  atomicMax(&p.parent[w], u);
+  if (nxt[ww] & m) return;
+  const uint32_t old = atomicOr(&nxt[ww], m);
+  if (old & m) return;
+  claim_topdown(p, k + 1, w, acc);
+}
+
+// Descending scan of one row for the first neighbour whose bit is set in `bm`
+// (= the largest-id neighbour in that set, rows being sorted ascending).
+__device__ __forceinline__ int scan_desc_thread(const int32_t* __restrict__ adj, long long b, long long e,
+                                                const uint32_t* bm) {
+  long long j = e - 1;
+  for (; j - 3 >= b; j -= 4) {
+    const int u0 = __ldg(&adj[j]), u1 = __ldg(&adj[j - 1]), u2 = __ldg(&adj[j - 2]), u3 = __ldg(&adj[j - 3]);
+    const uint32_t w0 = bm[u0 >> 5], w1 = bm[u1 >> 5], w2 = bm[u2 >> 5], w3 = bm[u3 >> 5];
+    if ((w0 >> (u0 & 31)) & 1u) return u0;
+    if ((w1 >> (u1 & 31)) & 1u) return u1;
+    if ((w2 >> (u2 & 31)) & 1u) return u2;
+    if ((w3 >> (u3 & 31)) & 1u) return u3;
+  }
+  for (; j >= b; --j) {
+    const int u = __ldg(&adj[j]);
+    if ((bm[u >> 5] >> (u & 31)) & 1u) return u;
+  }
+  return -1;
+}
+
+// Same scan done by a whole warp, 32 entries per step (all lanes call it).
+__device__ __forceinline__ int scan_desc_warp(const int32_t* __restrict__ adj, long long b, long long e,
+                                              const uint32_t* bm, int lane) {
+  for (long long top = e; top > b; top -= 32) {
+    const long long j = top - 1 - lane;
+    int u = 0;
+    bool h = false;
+    if (j >= b) {
+      u = __ldg(&adj[j]);
+      h = (bm[u >> 5] >> (u & 31)) & 1u;
+    }
+    const unsigned hm = __ballot_sync(kFull, h);
+    if (hm) return __shfl_sync(kFull, u, __ffs(hm) - 1);
+  }
+  return -1;
+}
+
+// 64-bit warp sum.
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Adds the CTA's accumulated counters into level knext's slot.
+__device__ __forceinline__ void flush_acc(const LoopParams& p, int knext, Acc& acc, unsigned long long* s_acc) {
+  const unsigned long long e = warp_sum_u64(acc.edges), b0 = warp_sum_u64(acc.b0), b1 = warp_sum_u64(acc.b1),
+                           b2 = warp_sum_u64(acc.b2);
+  if ((threadIdx.x & 31) == 0 && (e | b0 | b1 | b2)) {
+    atomicAdd(&s_acc[0], e);
+    atomicAdd(&s_acc[1], b0);
+    atomicAdd(&s_acc[2], b1);
+    atomicAdd(&s_acc[3], b2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    LevelCtr* c = &p.ctr[knext % kCtrRing];
+    if (s_acc[0]) atomicAdd(&c->edges, s_acc[0]);
+    if (s_acc[1]) atomicAdd(&c->bins[0], s_acc[1]);
+    if (s_acc[2]) atomicAdd(&c->bins[1], s_acc[2]);
+    if (s_acc[3]) atomicAdd(&c->bins[2], s_acc[3]);
+    s_acc[0] = s_acc[1] = s_acc[2] = s_acc[3] = 0;
+  }
+  acc = Acc{};
+}
+
+// Exclusive CTA-wide prefix sum of one int per thread; returns the total.
+__device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int& excl) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int v = lane < kWarps ? s_warp[lane] : 0;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane < kWarps) s_warp[lane] = inc - v;
+    if (lane == kWarps - 1) s_warp[kWarps] = inc;
+  }
+  __syncthreads();
+  excl = s_warp[wid] + incl - x;
+  const int total = s_warp[kWarps];
+  __syncthreads();
+  return total;
+}
+
+struct Smem {
+  int owner;
+  int cu;
+  long long cb, ce;
+  int warp_tmp[kWarps + 1];
+  unsigned long long acc[4];
+  int tu[kBlock];
+  long long tb[kBlock];
+  int tpref[kBlock + 1];
+  float x[12];
+  float h1[64];
+  float h2[64];
+  float y[4];
+  int choice;
+};
+
+// ---------------- top-down phase ----------------
+__device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned count, unsigned nchunks, Smem& sm,
+                              Acc& acc) {
+  const uint32_t* cur = p.bits[k % 3];
+  uint32_t* nxt = p.bits[(k + 1) % 3];
+  const int32_t* Q = p.queue[k % 3];
+  const int tid = threadIdx.x, lane = tid & 31;
+
+  // chunk items of high-degree frontier vertices: one CTA per item
+  const int64_t* items = p.chunks[k & 1];
+  for (unsigned ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+    const int64_t it = items[ci];
+    const int v = (int)(it >> 32);
+    const long long c = it & 0xffffffffll;
+    const long long rb = __ldg(&p.off[v]), re = __ldg(&p.off[v + 1]);
+    const long long b = rb + c * kChunkEdges;
+    const long long e = min(b + (long long)kChunkEdges, re);
+    for (long long j = b + tid; j < e; j += kBlock) td_visit(p, cur, nxt, k, v, __ldg(&p.adj[j]), acc);
+  }
+
+  const long long gthreads = (long long)gridDim.x * kBlock;
+  if (variant == BFS_VARIANT_TD_THREAD) {
+    for (long long i = (long long)blockIdx.x * kBlock + tid; i < count; i += gthreads) {
+      const int u = Q[i];
+      atomicOr(&p.vis[u >> 5], 1u << (u & 31));
+      const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
+      if (e - b > p.chunk_deg) continue;
+      for (long long j = b; j < e; ++j) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc);
+    }
+  } else if (variant == BFS_VARIANT_TD_WARP) {
+    const long long gwarps = gthreads / 32;
+    for (long long i = ((long long)blockIdx.x * kBlock + tid) / 32; i < count; i += gwarps) {
+      const int u = Q[i];
+      if (lane == 0) atomicOr(&p.vis[u >> 5], 1u << (u & 31));
+      const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
+      if (e - b > p.chunk_deg) continue;
+      for (long long j = b + lane; j < e; j += 32) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc);
+    }
+  } else {  // BFS_VARIANT_TD_BINNED
+    for (long long tile = (long long)blockIdx.x * kBlock; tile < count; tile += gthreads) {
+      const long long i = tile + tid;
+      int u = -1;
+      long long b = 0, e = 0;
+      if (i < count) {
+        u = Q[i];
+        atomicOr(&p.vis[u >> 5], 1u << (u & 31));
+        b = __ldg(&p.off[u]);
+        e = __ldg(&p.off[u + 1]);
+        if (e - b > p.chunk_deg) u = -1;
+      }
+      const long long deg = u >= 0 ? e - b : 0;
+      // CTA bin: the whole CTA walks one row at a time
+      for (;;) {
+        if (u >= 0 && deg >= p.cta_deg) sm.owner = tid;
+        __syncthreads();
+        const int owner = sm.owner;
+        if (owner < 0) break;
+        if (tid == owner) {
+          sm.cu = u;
+          sm.cb = b;
+          sm.ce = e;
+          u = -1;
+        }
+        __syncthreads();
+        const int cu = sm.cu;
+        const long long cb = sm.cb, ce = sm.ce;
+        for (long long j = cb + tid; j < ce; j += kBlock) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc);
+        __syncthreads();
+        if (tid == 0) sm.owner = -1;
+        __syncthreads();
+      }
+      // warp bin: a warp walks one row at a time
+      for (;;) {
+        const unsigned wm = __ballot_sync(kFull, u >= 0 && deg >= p.warp_deg);
+        if (!wm) break;
+        const int l = __ffs(wm) - 1;
+        const int cu = __shfl_sync(kFull, u, l);
+        const long long cb = __shfl_sync(kFull, b, l), ce = __shfl_sync(kFull, e, l);
+        if (lane == l) u = -1;
+        for (long long j = cb + lane; j < ce; j += 32) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc);
+      }
+      // thread bin: the CTA gathers the remaining short rows edge by edge
+      const int sdeg = u >= 0 ? (int)deg : 0;
+      int excl = 0;
+      const int total = block_exclusive_scan(sdeg, sm.warp_tmp, excl);
+      sm.tu[tid] = u;
+      sm.tb[tid] = b;
+      sm.tpref[tid] = excl;
+      if (tid == 0) sm.tpref[kBlock] = total;
+      __syncthreads();
+      for (int base = 0; base < total; base += kBlock) {
+        const int idx = base + tid;
+        if (idx < total) {
+          int lo = 0, hi = kBlock;  // largest slot with tpref <= idx (and a non-empty row)
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.tpref[mid] <= idx) lo = mid;
+            else hi = mid;
+          }
+          const int ou = sm.tu[lo];
+          td_visit(p, cur, nxt, k, ou, __ldg(&p.adj[sm.tb[lo] + (idx - sm.tpref[lo])]), acc);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------- pull phase ----------------
+__device__ void pull_phase(const LoopParams& p, int k, Acc& acc) {
+  const uint32_t* cur = p.bits[k % 3];
+  uint32_t* nxt = p.bits[(k + 1) % 3];
+  int32_t* NQ = p.queue[(k + 1) % 3];
+  const int lane = threadIdx.x & 31;
+  const long long gwarps = (long long)gridDim.x * kWarps;
+  const int knext = k + 1;
+  for (long long ww = ((long long)blockIdx.x * kBlock + threadIdx.x) / 32; ww < p.nwords; ww += gwarps) {
+    const uint32_t vw = p.vis[ww];
+    const uint32_t visw = vw | cur[ww];
+    if (visw == 0xffffffffu) {  // nothing to pull, but vis must absorb f_k's bits
+      if (lane == 0 && vw != visw) p.vis[ww] = visw;
+      continue;
+    }
+    const int v = (int)(ww * 32 + lane);
+    const bool active = !((visw >> lane) & 1u);
+    long long b = 0, e = 0;
+    if (active) {
+      b = __ldg(&p.off[v]);
+      e = __ldg(&p.off[v + 1]);
+    }
+    const long long deg = e - b;
+    int hit = -1;
+    const bool longrow = active && deg > p.pull_thread_deg;
+    if (active && !longrow) hit = scan_desc_thread(p.adj, b, e, cur);
+    unsigned lm = __ballot_sync(kFull, longrow);
+    while (lm) {
+      const int l = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const long long lb = __shfl_sync(kFull, b, l), le = __shfl_sync(kFull, e, l);
+      const int h = scan_desc_warp(p.adj, lb, le, cur, lane);
+      if (lane == l) hit = h;
+    }
+    const unsigned hits = __ballot_sync(kFull, hit >= 0);
+    if (lane == 0) {
+      if (hits) nxt[ww] = hits;
+      p.vis[ww] = visw | hits;
+    }
+    if (!hits) continue;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)__popc(hits));
+    base = __shfl_sync(kFull, base, 0);
+    if (hit >= 0) {
+      p.parent[v] = hit;
+      p.level[v] = knext;
+      NQ[base + __popc(hits & bfsdev::lanemask_lt())] = v;
+      acc_vertex(acc, deg);
+      if (deg > p.chunk_deg) push_chunks(p, knext, v, deg);
+    }
+  }
+}
+
+__device__ __forceinline__ int heuristic_variant(const LoopParams& p, int prev_variant, long long count,
+                                                 long long edges, long long unvisited_edges,
+                                                 const long long* bins) {
+  bool pull;
+  if (prev_variant == BFS_VARIANT_PULL) pull = (float)count * p.beta >= (float)p.n;
+  else pull = (float)edges * p.alpha > (float)unvisited_edges;
+  if (pull) return BFS_VARIANT_PULL;
+  if (bins[1] + bins[2] == 0) return BFS_VARIANT_TD_THREAD;
+  return BFS_VARIANT_TD_BINNED;
+}
+
+__global__ void __launch_bounds__(kBlock) level_loop_kernel(LoopParams p) {
+  __shared__ Smem sm;
+  extern __shared__ float s_mlp[];  // BFS_MLP_PARAMS floats when the learned selector is on
+  const int tid = threadIdx.x;
+  unsigned epoch = 0;
+  if (tid == 0) {
+    epoch = bfsdev::ld_acquire_u32(&p.bar->epoch);
+    sm.owner = -1;
+    sm.acc[0] = sm.acc[1] = sm.acc[2] = sm.acc[3] = 0;
+  }
+  const bool learned = p.selector == BFS_SELECT_LEARNED && p.mlp != nullptr;
+  if (learned)
+    for (int i = tid; i < BFS_MLP_PARAMS; i += kBlock) s_mlp[i] = p.mlp[i];
+
+  const long long gtid = (long long)blockIdx.x * kBlock + tid;
+  const long long gthreads = (long long)gridDim.x * kBlock;
+  const unsigned nblocks = gridDim.x;
+
+  // ---- init: outputs to -1, bitmaps cleared (tail bits of vis set), counters zeroed
+  for (long long v = gtid; v < p.n; v += gthreads) {
+    p.level[v] = -1;
+    p.parent[v] = -1;
+  }
+  const uint32_t tail = (p.n & 31) ? ~((1u << (p.n & 31)) - 1u) : 0u;
+  for (long long w = gtid; w < p.nwords; w += gthreads) {
+    p.bits[0][w] = 0;
+    p.bits[1][w] = 0;
+    p.bits[2][w] = 0;
+    p.vis[w] = (w == p.nwords - 1) ? tail : 0u;
+  }
+  if (blockIdx.x == 0 && tid < kCtrRing * (int)(sizeof(LevelCtr) / 8))
+    reinterpret_cast<unsigned long long*>(p.ctr)[tid] = 0ull;
+  if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+
+  // ---- seed level 0 with the sources (block 0)
+  if (blockIdx.x == 0) {
+    Acc acc;
+    for (int i = tid; i < p.nsources; i += kBlock) {
+      const int s = p.nsources == 1 ? p.src0 : p.sources[i];
+      p.level[s] = 0;
+      p.parent[s] = s;
+      atomicOr(&p.bits[0][s >> 5], 1u << (s & 31));
+      p.queue[0][i] = s;
+      const long long deg = __ldg(&p.off[s + 1]) - __ldg(&p.off[s]);
+      acc_vertex(acc, deg);
+      if (deg > p.chunk_deg) push_chunks(p, 0, s, deg);
+    }
+    if (tid == 0) p.ctr[0].count = (unsigned)p.nsources;
+    flush_acc(p, 0, acc, sm.acc);
+  }
+  if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+
+  // ---- level loop
+  long long cum_count = 0, cum_edges = 0;
+  int prev_variant = -1;
+  uint64_t t_prev = 0;
+  if (blockIdx.x == 0 && tid == 0) t_prev = bfsdev::global_timer_ns();
+  int k = 0;
+  Acc acc;
+  for (;; ++k) {
+    const LevelCtr* c = &p.ctr[k % kCtrRing];
+    const unsigned count = __ldcg(&c->count);
+    if (count == 0) break;
+    const unsigned nchunks = __ldcg(&c->chunks);
+    const long long edges = (long long)__ldcg(&c->edges);
+    long long bins[3] = {(long long)__ldcg(&c->bins[0]), (long long)__ldcg(&c->bins[1]),
+                         (long long)__ldcg(&c->bins[2])};
+    cum_count += count;
+    cum_edges += edges;
+    const long long unvisited = (long long)p.n - cum_count;
+    const long long unvisited_edges = p.nnz - cum_edges;
+
+    int variant;
+    if (p.selector == BFS_SELECT_FORCED) {
+      variant = p.forced;
+    } else if (p.selector == BFS_SELECT_SCHEDULE && k < p.schedule_len) {
+      variant = p.schedule[k];
+    } else if (learned) {
+      if (tid == 0)
+        bfsdev::level_features(p.n, p.nnz, k, count, edges, unvisited, unvisited_edges, bins, sm.x);
+      __syncthreads();
+      if (tid < 64) sm.h1[tid] = bfsdev::mlp_h1(s_mlp, sm.x, tid);
+      __syncthreads();
+      if (tid < 64) sm.h2[tid] = bfsdev::mlp_h2(s_mlp, sm.h1, tid);
+      __syncthreads();
+      if (tid < 4) sm.y[tid] = bfsdev::mlp_out(s_mlp, sm.h2, tid);
+      __syncthreads();
+      if (tid == 0) {
+        int best = 0;
+        for (int o = 1; o < 4; ++o)
+          if (sm.y[o] < sm.y[best]) best = o;
+        sm.choice = best;
+      }
+      __syncthreads();
+      variant = sm.choice;
+    } else {
+      variant = heuristic_variant(p, prev_variant, count, edges, unvisited_edges, bins);
+    }
+    if (variant < 0 || variant >= BFS_NUM_VARIANTS) variant = BFS_VARIANT_TD_BINNED;
+
+    // recycle: counters of level k+4, bitmap of level k-1
+    if (blockIdx.x == 0 && tid < (int)(sizeof(LevelCtr) / 8))
+      reinterpret_cast<unsigned long long*>(&p.ctr[(k + 4) % kCtrRing])[tid] = 0ull;
+    if (k >= 1) {
+      uint32_t* clr = p.bits[(k + 2) % 3];
+      const unsigned prev_count = __ldcg(&p.ctr[(k + kCtrRing - 1) % kCtrRing].count);
+      if ((long long)prev_count * 4 < p.nwords) {
+        const int32_t* PQ = p.queue[(k + 2) % 3];
+        for (long long i = gtid; i < prev_count; i += gthreads) clr[PQ[i] >> 5] = 0u;
+      } else {
+        for (long long w = gtid; w < p.nwords; w += gthreads) clr[w] = 0u;
+      }
+    }
+
+    if (variant == BFS_VARIANT_PULL) pull_phase(p, k, acc);
+    else topdown_phase(p, k, variant, count, nchunks, sm, acc);
+    flush_acc(p, k + 1, acc, sm.acc);
+    if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+
+    if (p.want_stats && blockIdx.x == 0 && tid == 0 && k < kMaxStatLevels) {
+      const uint64_t t = bfsdev::global_timer_ns();
+      bfs_level_stat st;
+      st.frontier_count = count;
+      st.frontier_edges = edges;
+      st.bin_count[0] = bins[0];
+      st.bin_count[1] = bins[1];
+      st.bin_count[2] = bins[2];
+      st.unvisited_count = unvisited;
+      st.unvisited_edges = unvisited_edges;
+      st.time_ns = (int64_t)(t - t_prev);
+      st.variant = variant;
+      st.reserved = 0;
+      p.stats[k] = st;
+      t_prev = t;
+    }
+    prev_variant = variant;
+  }
+
+  if (gtid == 0) {
+    p.misc[0] = k;
+    *p.edges_out = cum_edges / 2;
+  }
+  // ragged: copy the union-space outputs into each part's arrays, local ids
+  if (p.part_out != nullptr) {
+    for (int q = 0; q < p.parts; ++q) {
+      const long long base = p.part_base[q], size = p.part_base[q + 1] - base;
+      int32_t* lo = p.part_out[q];
+      int32_t* po = p.part_out[p.parts + q];
+      for (long long v = gtid; v < size; v += gthreads) {
+        lo[v] = p.level[base + v];
+        const int par = p.parent[base + v];
+        po[v] = par >= 0 ? (int)(par - base) : -1;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int launch_level_loop(const RunRequest& r, cudaStream_t s) {
+  bfs_graph* g = r.g;
+  Workspace* w = r.w;
+  DeviceInfo di;
+  if (int e = current_device_info(&di)) return e;
+  if (r.nsources < 1 || r.nsources > kMaxSources) return fail(BFS_ERR_INVALID_ARG, "number of sources out of range");
+  int sched_len = 0;
+  const bool need_sched = r.selector == BFS_SELECT_SCHEDULE && r.h_schedule && r.schedule_len > 0;
+  if (r.nsources > 1 || need_sched) {  // stage through pinned memory (no pageable-copy synchronisation)
+    if (int e = stage_wait(w)) return e;
+    if (r.nsources > 1) {
+      std::copy(r.h_sources, r.h_sources + r.nsources, w->h_stage + kMaxSchedule);
+      BFS_CUDA_TRY(cudaMemcpyAsync(w->sources, w->h_stage + kMaxSchedule, sizeof(int32_t) * r.nsources,
+                                   cudaMemcpyHostToDevice, s));
+    }
+    if (need_sched) {
+      sched_len = r.schedule_len < kMaxSchedule ? r.schedule_len : kMaxSchedule;
+      std::copy(r.h_schedule, r.h_schedule + sched_len, w->h_stage);
+      BFS_CUDA_TRY(cudaMemcpyAsync(w->schedule, w->h_stage, sizeof(int32_t) * sched_len, cudaMemcpyHostToDevice, s));
+    }
+    BFS_CUDA_TRY(cudaEventRecord(w->stage_ev, s));
+  }
+  const bfs_tuning t = effective_tuning(g);
+  LoopParams p{};
+  p.off = g->d_off;
+  p.adj = g->d_adj;
+  p.n = g->n;
+  p.nwords = w->nwords;
+  p.nnz = g->nnz;
+  p.level = r.level;
+  p.parent = r.parent;
+  for (int i = 0; i < 3; ++i) {
+    p.queue[i] = w->queue[i];
+    p.bits[i] = w->bits[i];
+  }
+  p.vis = w->vis;
+  p.chunks[0] = w->chunks[0];
+  p.chunks[1] = w->chunks[1];
+  p.ctr = w->ctr;
+  p.bar = reinterpret_cast<bfsdev::GridBarrier*>(w->barrier);
+  p.status = w->status;
+  p.stats = w->stats;
+  p.misc = w->misc;
+  p.edges_out = w->edges_out;
+  p.sources = w->sources;
+  p.src0 = r.h_sources[0];
+  p.nsources = r.nsources;
+  p.selector = r.selector;
+  p.forced = r.forced;
+  p.schedule = w->schedule;
+  p.schedule_len = sched_len;
+  p.mlp = r.selector == BFS_SELECT_LEARNED ? learned_params_device() : nullptr;
+  p.want_stats = r.want_stats ? 1 : 0;
+  p.spin_limit = r.spin_limit ? r.spin_limit : (1u << 25);
+  p.warp_deg = t.warp_degree;
+  p.cta_deg = t.cta_degree;
+  p.pull_thread_deg = t.pull_thread_degree;
+  p.chunk_deg = t.chunk_degree;
+  p.alpha = t.alpha;
+  p.beta = t.beta;
+  p.parts = g->parts;
+  p.part_base = g->d_part_base;
+  p.part_out = r.part_out;
+
+  const size_t dyn_smem = p.mlp ? sizeof(float) * BFS_MLP_PARAMS : 0;
+  static int configured = 0;
+  if (!configured) {
+    BFS_CUDA_TRY(cudaFuncSetAttribute(level_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(float) * BFS_MLP_PARAMS)));
+    configured = 1;
+  }
+  int per_sm = 0;
+  BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_loop_kernel, kBlock, dyn_smem));
+  if (per_sm < 1) return fail(BFS_ERR_CUDA, "level loop kernel cannot be resident");
+  const int grid = per_sm * di.sm_count;
+  void* args[] = {&p};
+  BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)level_loop_kernel, dim3(grid), dim3(kBlock), args,
+                                           dyn_smem, s));
+  return BFS_OK;
+}
+
+}  // namespace bfsint

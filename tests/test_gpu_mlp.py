@@ -1,0 +1,138 @@
+"""GPU selector network vs the float64 oracle: forward, loss, gradient, Adam, training,
+the in-loop features and the learned selector inside a traversal.
+
+Tolerance: float32 kernels against float64 arithmetic on the same float32 inputs.
+Each output is a dot product of at most 64 terms of magnitude <= ~1 passed through
+three layers; float32 rounding (2^-24 relative per operation) accumulated over
+~200 dependent operations stays below 1e-5 relative, so forward outputs are
+checked at rtol 1e-5 / atol 1e-5, and gradients (sums over a batch of such terms)
+at rtol 1e-4 / atol 1e-6."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp
+import paper_1104_4518_gb300 as bfs
+from gpu_helpers import assert_same, device_graph_from_edges, require_cuda
+from paper_1104_4518_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    require_cuda()
+
+
+def params32(seed):
+    rng = np.random.default_rng(seed)
+    return (mlp.he_uniform_init(rng.random(mlp.N_PARAMS)) + 0.02 * rng.standard_normal(mlp.N_PARAMS)).astype(np.float32)
+
+
+def data(seed, B):
+    rng = np.random.default_rng(seed)
+    X = rng.random((B, 12)).astype(np.float32)
+    T = (3 * rng.standard_normal((B, 4))).astype(np.float32)
+    return X, T
+
+
+@pytest.mark.parametrize("B", [1, 31, 32, 33, 1000])
+def test_forward(B):
+    w = params32(B)
+    X, _ = data(B + 1, B)
+    Y = torch.empty((B, 4), dtype=torch.float32, device="cuda")
+    bfs.bfs_mlp_forward(torch.from_numpy(w).cuda(), torch.from_numpy(X).cuda(), Y)
+    ref, _ = mlp.forward(w.astype(np.float64), X.astype(np.float64))
+    np.testing.assert_allclose(Y.cpu().numpy(), ref, rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.parametrize("B", [1, 32, 77, 2048])
+def test_loss_and_gradient(B):
+    w = params32(10 + B)
+    X, T = data(20 + B, B)
+    grad = torch.empty(mlp.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    bfs.bfs_mlp_loss_grad(torch.from_numpy(w).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(),
+                          grad, loss)
+    ref_loss, ref_grad = mlp.loss_and_grad(w.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    np.testing.assert_allclose(loss.item(), ref_loss, rtol=1e-5)
+    np.testing.assert_allclose(grad.cpu().numpy(), ref_grad, rtol=1e-4, atol=1e-6)
+    # deterministic: a second evaluation is bit-identical
+    g2 = torch.empty_like(grad)
+    bfs.bfs_mlp_loss_grad(torch.from_numpy(w).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(),
+                          g2, None)
+    assert torch.equal(grad, g2)
+
+
+def test_adam_steps():
+    rng = np.random.default_rng(3)
+    w = params32(3)
+    p = torch.from_numpy(w).cuda()
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    wr, mr, vr = w.astype(np.float64), np.zeros(mlp.N_PARAMS), np.zeros(mlp.N_PARAMS)
+    for t in range(1, 6):
+        g = rng.standard_normal(mlp.N_PARAMS).astype(np.float32)
+        bfs.bfs_mlp_adam(p, torch.from_numpy(g).cuda(), m, v, t, lr=1e-2)
+        wr, mr, vr = mlp.adam_step(wr, g.astype(np.float64), mr, vr, t, lr=1e-2)
+    np.testing.assert_allclose(p.cpu().numpy(), wr, rtol=1e-5, atol=1e-6)
+
+
+def test_training_matches_oracle_and_reduces_loss():
+    w = params32(4)
+    X, _ = data(5, 256)
+    # a learnable target: a fixed linear map of the inputs
+    A = np.random.default_rng(6).standard_normal((12, 4)).astype(np.float32)
+    T = (X @ A).astype(np.float32)
+    p = torch.from_numpy(w).cuda()
+    hist = torch.empty(50, dtype=torch.float32, device="cuda")
+    bfs.bfs_selector_train(p, torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), 50, lr=1e-2, loss_history=hist)
+    # oracle: same 50 full-batch Adam steps in float64
+    wr, mr, vr = w.astype(np.float64), np.zeros(mlp.N_PARAMS), np.zeros(mlp.N_PARAMS)
+    losses = []
+    for t in range(1, 51):
+        L, g = mlp.loss_and_grad(wr, X.astype(np.float64), T.astype(np.float64))
+        losses.append(L)
+        wr, mr, vr = mlp.adam_step(wr, g, mr, vr, t, lr=1e-2)
+    h = hist.cpu().numpy()
+    assert h[-1] < 0.5 * h[0]
+    np.testing.assert_allclose(h, losses, rtol=2e-3)
+    np.testing.assert_allclose(p.cpu().numpy(), wr, rtol=1e-2, atol=2e-4)
+
+
+def test_level_features_host_vs_oracle():
+    args = dict(n=1 << 20, nnz=33_554_000, k=3, f_count=12345, f_edges=987654, unvisited=400_000,
+                unvisited_edges=20_000_000, bin_counts=(10000, 2300, 45))
+    got = bfs.bfs_level_features(args["n"], args["nnz"], args["k"], args["f_count"], args["f_edges"],
+                                 args["unvisited"], args["unvisited_edges"], args["bin_counts"])
+    ref = mlp.features(**args)
+    np.testing.assert_allclose(got, ref, rtol=1e-6, atol=1e-7)
+
+
+def test_learned_selector_in_traversal():
+    """The in-loop network picks variants; results stay identical, and the variants it
+    picks are the argmin of the forward kernel on the recorded features."""
+    el, roots = inputs.workload_rmat(16, 4, graph_seed=1, root_seed=101)
+    og = oracle.csr_of(el)
+    g = device_graph_from_edges(el)
+    w = params32(7)
+    bfs.bfs_selector_set_params(w)
+    try:
+        for s in roots:
+            opts = bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED, stats_levels=64)
+            parent, level = bfs.run(g, int(s), opts)
+            assert_same(oracle.bfs(og, int(s)), (level.cpu().numpy(), parent.cpu().numpy()))
+            st = opts.stats()
+            feats = np.stack([bfs.bfs_level_features(og.n, og.nnz, k, x["frontier_count"], x["frontier_edges"],
+                                                     x["unvisited_count"], x["unvisited_edges"], x["bin_count"])
+                              for k, x in enumerate(st)])
+            Y = torch.empty((len(st), 4), dtype=torch.float32, device="cuda")
+            bfs.bfs_mlp_forward(torch.from_numpy(w).cuda(), torch.from_numpy(feats).cuda(), Y)
+            Yh = Y.cpu().numpy()
+            for k, x in enumerate(st):
+                srt = np.sort(Yh[k])
+                if srt[1] - srt[0] > 1e-4:  # a clear argmin (features may differ by an ulp of log2f)
+                    assert x["variant"] == int(np.argmin(Yh[k]))
+    finally:
+        bfs.bfs_selector_set_params(None)
