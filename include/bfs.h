@@ -198,6 +198,30 @@ BFS_API int bfs_run_batch(bfs_graph* g, const int32_t* sources, int32_t k, int32
 BFS_API int bfs_run_ragged(bfs_graph* u, const int32_t* sources, int32_t* const* parent_out,
                    int32_t* const* level_out, const bfs_opts* opts, void* stream);
 
+/*
+ * Single-source BFS that allocates nothing (the paper has no counterpart: this
+ * entry point exists for callers of this library that cannot call cudaMalloc,
+ * for example a plug-in or a real-time loop that must not trigger the device
+ * synchronisation and the possible failure of an allocation, or a process
+ * whose device memory was reserved up front by another allocator).
+ * The caller passes the CSR (offsets int64[n+1], adj int32[nnz], device
+ * memory, rows sorted, each undirected edge in both rows, not validated) and
+ * the outputs parent_out / level_out (device int32[n]); results are those of
+ * bfs_run with the heuristic selector.  All scratch memory of the traversal
+ * (about 13.2 MB) is one static array inside the library, which every GPU that
+ * loads the library holds until the process exits; hence the limits
+ * n <= 1,048,576 and nnz <= 67,108,864, beyond which the call returns
+ * BFS_ERR_INVALID_ARG.  The first call on a device sets up that device (looks
+ * up the array's device address and clears its barrier and status words), so
+ * it should come before any stream capture.  Every call shares the array and
+ * finds the previous call's contents there (the traversal re-initialises what
+ * it needs), so calls that overlap on the GPU race: issue one at a time per
+ * device.  The call waits for `stream` to finish the traversal and returns its
+ * device status (BFS_ERR_TIMEOUT if a device-side wait reached its limit).
+ */
+BFS_API int bfs_run_static(const int64_t* offsets, const int32_t* adj, int32_t n, int64_t nnz, int32_t source,
+                           int32_t* parent_out, int32_t* level_out, void* stream);
+
 /* Waits for the stream and returns (and clears) the device status of the last
  * run enqueued on it for graph g. */
 BFS_API int bfs_sync(bfs_graph* g, void* stream);

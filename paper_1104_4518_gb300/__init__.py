@@ -101,6 +101,7 @@ def _declare(lib):
         "bfs_run_ragged": [vp, ctypes.POINTER(i32), ctypes.POINTER(vp), ctypes.POINTER(vp),
                            ctypes.POINTER(bfs_opts), vp],
         "bfs_sync": [vp, vp],
+        "bfs_run_static": [vp, vp, i32, i64, i32, vp, vp, vp],
         "bfs_set_tuning": [vp, ctypes.POINTER(bfs_tuning)],
         "bfs_get_tuning": [vp, ctypes.POINTER(bfs_tuning)],
         "bfs_autotune": [vp, ctypes.POINTER(i32), i32, ctypes.POINTER(bfs_tuning), vp],
@@ -341,6 +342,14 @@ def bfs_run_ragged(u: Graph, sources, parent_outs, level_outs, opts: RunOptions 
     la = (ctypes.c_void_p * len(level_outs))(*[_ptr_and_host(t, "int32")[0] for t in level_outs])
     _check(lib().bfs_run_ragged(u.handle, src.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), pa, la,
                                 _opts_ptr(opts), _stream_handle(stream)))
+
+
+def bfs_run_static(offsets, adj, source: int, parent_out, level_out, stream=None):
+    """BFS that allocates nothing: CSR and outputs are caller device tensors; the
+    library's scratch is a fixed static array (n <= 1,048,576, nnz <= 67,108,864).
+    Synchronous; raises on a device-side timeout."""
+    _check(lib().bfs_run_static(offsets.data_ptr(), adj.data_ptr(), int(offsets.shape[0]) - 1, int(adj.shape[0]),
+                                int(source), parent_out.data_ptr(), level_out.data_ptr(), _stream_handle(stream)))
 
 
 def bfs_sync(g: Graph, stream=None):
