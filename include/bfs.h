@@ -91,9 +91,11 @@ typedef struct bfs_level_stat {
 /* Tuning knobs (bfs_autotune fills them; zero fields mean "library default"). */
 typedef struct bfs_tuning {
   int32_t warp_degree;   /* TD_BINNED: degree from which a vertex gets a warp (default 32) */
-  int32_t cta_degree;    /* TD_BINNED: degree from which a vertex gets a CTA (default 1024) */
-  int32_t pull_thread_degree; /* PULL: rows up to this degree are scanned by one thread (default 32) */
-  int32_t chunk_degree;  /* top-down: vertices above this degree are split into grid-wide chunks (default 16384) */
+  int32_t cta_degree;    /* TD_BINNED: degree from which a vertex gets a CTA (default 256) */
+  int32_t pull_thread_degree; /* PULL: top entries of a row each lane tests alone before the warp-wide scan
+                                 (1..8, default 4) */
+  int32_t chunk_degree;  /* top-down: vertices above this degree are split into grid-wide chunks of 1024
+                            edges (>= 1024, default 1024) */
   float alpha;           /* heuristic: go PULL when frontier edges > unvisited edges / alpha (default 14) */
   float beta;            /* heuristic: leave PULL when frontier count < n / beta (default 24) */
   int32_t batch_topdown_limit; /* batched: levels with at most this many active vertices expand top-down (default n/64) */
@@ -181,7 +183,10 @@ BFS_API int bfs_run(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* 
  * matrix-dense matrix product per level); parents follow the same max-id rule,
  * recovered by scanning each newly reached vertex's row from the largest id
  * down.  k > 64 runs in chunks of 64.  Results equal k calls of bfs_run.
- * Only the heuristic choice between top-down and pull per level applies.
+ * Each level expands top-down when its frontier has at most
+ * bfs_tuning.batch_topdown_limit vertices, by pull otherwise.  With
+ * opts->stats, the levels of the last chunk are reported (frontier_count,
+ * time_ns, variant BFS_VARIANT_TD_WARP or BFS_VARIANT_PULL).
  */
 BFS_API int bfs_run_batch(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* parent_out,
                   int32_t* level_out, const bfs_opts* opts, void* stream);
@@ -208,7 +213,7 @@ BFS_API int bfs_run_ragged(bfs_graph* u, const int32_t* sources, int32_t* const*
  * memory, rows sorted, each undirected edge in both rows, not validated) and
  * the outputs parent_out / level_out (device int32[n]); results are those of
  * bfs_run with the heuristic selector.  All scratch memory of the traversal
- * (about 13.2 MB) is one static array inside the library, which every GPU that
+ * (about 15.3 MB) is one static array inside the library, which every GPU that
  * loads the library holds until the process exits; hence the limits
  * n <= 1,048,576 and nnz <= 67,108,864, beyond which the call returns
  * BFS_ERR_INVALID_ARG.  The first call on a device sets up that device (looks
@@ -268,6 +273,20 @@ BFS_API int bfs_mlp_adam(float* params, const float* grad, float* m, float* v, i
  * place; loss_history (device float[steps]) may be NULL. */
 BFS_API int bfs_selector_train(float* params, const float* X, const float* T, int32_t B, int32_t steps,
                        float lr, float* loss_history, void* stream);
+
+/*
+ * Training samples for the selector network from traversals of graph g: for
+ * every root (host array) the traversal runs `reps` times with each variant
+ * forced at every level, and for every level k one row is written:
+ * X[row][0..11] = the level's features (bfs_level_features) and
+ * T[row][v] = log2 of the median time in microseconds of level k under
+ * variant v (host float arrays of max_rows rows).  *rows_out receives the
+ * number of rows written (rows beyond max_rows are dropped).  Levels and
+ * parents do not depend on the variant, so every run sees the same level
+ * sequence.  Synchronises the stream.
+ */
+BFS_API int bfs_selector_collect(bfs_graph* g, const int32_t* roots, int32_t nroots, int32_t reps, float* X, float* T,
+                                 int32_t max_rows, int32_t* rows_out, void* stream);
 
 /* Sets (params != NULL, host float[5252]) or clears (NULL) the network used by
  * BFS_SELECT_LEARNED in this process. */

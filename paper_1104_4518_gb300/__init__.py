@@ -109,6 +109,7 @@ def _declare(lib):
         "bfs_mlp_loss_grad": [vp, vp, vp, i32, vp, vp, vp],
         "bfs_mlp_adam": [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp],
         "bfs_selector_train": [vp, vp, vp, i32, i32, f32, vp, vp],
+        "bfs_selector_collect": [vp, ctypes.POINTER(i32), i32, i32, vp, vp, i32, ctypes.POINTER(i32), vp],
         "bfs_selector_set_params": [vp],
         "bfs_selector_load": [ctypes.c_char_p],
         "bfs_selector_save": [ctypes.c_char_p],
@@ -400,6 +401,18 @@ def bfs_selector_train(params, X, T, steps: int, lr: float = 1e-3, loss_history=
     _check(lib().bfs_selector_train(params.data_ptr(), X.data_ptr(), T.data_ptr(), int(X.shape[0]), int(steps),
                                     float(lr), loss_history.data_ptr() if loss_history is not None else None,
                                     _stream_handle(stream)))
+
+
+def bfs_selector_collect(g: Graph, roots, reps: int = 3, max_rows: int = 65536, stream=None):
+    """Per-level training rows (features X [rows,12], log2 level-time targets T [rows,4])."""
+    r = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
+    X = np.zeros((max_rows, BFS_MLP_IN), dtype=np.float32)
+    T = np.zeros((max_rows, BFS_MLP_OUT), dtype=np.float32)
+    rows = ctypes.c_int32(0)
+    _check(lib().bfs_selector_collect(g.handle, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(r.shape[0]),
+                                      int(reps), X.ctypes.data, T.ctypes.data, max_rows, ctypes.byref(rows),
+                                      _stream_handle(stream)))
+    return X[:rows.value].copy(), T[:rows.value].copy()
 
 
 def bfs_selector_set_params(params):

@@ -43,9 +43,13 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
-          ptxas_verbose: bool = False) -> str:
-    """Compiles and links the library if any source is newer than it; returns its path."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+          ptxas_verbose: bool = False, lib_path: str = LIB, build_dir: str = BUILD_DIR) -> str:
+    """Compiles and links the library if any source is newer than it; returns its path.
+
+    `extra_flags`, `lib_path` and `build_dir` let a diagnostic variant be built
+    elsewhere without touching the product library."""
+    LIB_OUT = lib_path
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "bfs.h"))
     srcs = sources()
@@ -53,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     objs = []
     jobs = []
     for src in srcs:
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             jobs.append([nvcc(), *ARCH, *flags, "-c", src, "-o", obj])
@@ -70,15 +74,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             sys.stderr.write(f"$ {' '.join(c)}\n{r.stdout}{r.stderr}")
     if failed:
         raise RuntimeError(f"nvcc failed for {[os.path.basename(c[-3]) for c, _ in failed]}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(LIB_OUT, objs):
+        tmp = LIB_OUT + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(f"$ {' '.join(cmd)}\n{r.stdout}{r.stderr}")
             raise RuntimeError("linking libbfs_gb300.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, LIB_OUT)
+    return LIB_OUT
 
 
 if __name__ == "__main__":

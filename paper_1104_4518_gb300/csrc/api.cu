@@ -2,6 +2,7 @@
 // library (graph copies, per-stream workspaces), and the host side of every
 // entry point declared in include/bfs.h.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -69,10 +70,11 @@ int current_device_info(DeviceInfo* out) {
 bfs_tuning effective_tuning(const bfs_graph* g) {
   bfs_tuning t = g->tuning;
   if (t.warp_degree <= 0) t.warp_degree = 32;
-  if (t.cta_degree <= 0) t.cta_degree = 1024;
+  if (t.cta_degree <= 0) t.cta_degree = 256;
   if (t.cta_degree < t.warp_degree) t.cta_degree = t.warp_degree;
-  if (t.pull_thread_degree <= 0) t.pull_thread_degree = 32;
-  if (t.chunk_degree <= 0) t.chunk_degree = 16384;
+  if (t.pull_thread_degree <= 0) t.pull_thread_degree = 4;
+  if (t.pull_thread_degree > 8) t.pull_thread_degree = 8;
+  if (t.chunk_degree <= 0) t.chunk_degree = 1024;
   if (t.chunk_degree < kChunkEdges) t.chunk_degree = kChunkEdges;
   if (!(t.alpha > 0.0f)) t.alpha = 14.0f;
   if (!(t.beta > 0.0f)) t.beta = 24.0f;
@@ -201,6 +203,18 @@ static int make_graph_from_device_csr(int64_t* d_off, int32_t* d_adj, int32_t n,
     cudaFree(g->d_part_base);
     delete g;
     return cuda_fail(err, "part table copy");
+  }
+  int rc = dev_alloc((void**)&g->d_dead, sizeof(uint32_t) * (((size_t)n + 31) / 32), "edgeless-vertex bitmap");
+  if (!rc) rc = compute_dead_bits(d_off, n, g->d_dead, nullptr);
+  if (!rc) {
+    err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) rc = cuda_fail(err, "edgeless-vertex bitmap");
+  }
+  if (rc) {
+    if (g->d_dead) cudaFree(g->d_dead);
+    cudaFree(g->d_part_base);
+    delete g;
+    return rc;
   }
   *out = g;
   return BFS_OK;
@@ -387,6 +401,7 @@ void bfs_graph_destroy(bfs_graph* g) {
   if (g->d_off) cudaFree(g->d_off);
   if (g->d_adj) cudaFree(g->d_adj);
   if (g->d_part_base) cudaFree(g->d_part_base);
+  if (g->d_dead) cudaFree(g->d_dead);
   delete g;
 }
 
@@ -490,6 +505,7 @@ int bfs_run_batch(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* pare
     br.level = host ? dl : level_out + (size_t)c * n;
     br.parent = host ? dp : parent_out + (size_t)c * n;
     br.spin_limit = opts ? opts->spin_limit : 0;
+    br.want_stats = opts && opts->stats && c + 64 >= k;  // statistics of the last chunk
     rc = launch_batch(br, s);
     if (!rc && host) {
       cudaError_t err = cudaMemcpyAsync(level_out + (size_t)c * n, dl, sizeof(int32_t) * n * br.k,
@@ -505,12 +521,15 @@ int bfs_run_batch(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* pare
     cudaFree(dl);
   }
   if (rc) return rc;
-  if (opts && (host || opts->nlevels_out)) {
+  if (opts && (host || opts->nlevels_out || opts->stats)) {
     if (int e = read_status(w, s)) return e;
-    if (opts->nlevels_out) {
-      int32_t nl = 0;
-      BFS_CUDA_TRY(cudaMemcpy(&nl, w->misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
-      *opts->nlevels_out = nl;
+    int32_t nl = 0;
+    BFS_CUDA_TRY(cudaMemcpy(&nl, w->misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (opts->nlevels_out) *opts->nlevels_out = nl;
+    if (opts->stats && opts->max_stat_levels > 0) {
+      const int cnt = std::min(std::min(nl, opts->max_stat_levels), kMaxStatLevels);
+      if (cnt > 0)
+        BFS_CUDA_TRY(cudaMemcpy(opts->stats, w->stats, sizeof(bfs_level_stat) * cnt, cudaMemcpyDeviceToHost));
     }
   }
   return BFS_OK;
@@ -587,6 +606,67 @@ int bfs_get_tuning(const bfs_graph* g, bfs_tuning* t) {
   return BFS_OK;
 }
 
+int bfs_selector_collect(bfs_graph* g, const int32_t* roots, int32_t nroots, int32_t reps, float* X, float* T,
+                         int32_t max_rows, int32_t* rows_out, void* stream) {
+  if (int e = check_graph(g)) return e;
+  if (!roots || nroots < 1 || reps < 1 || !X || !T || max_rows < 0 || !rows_out)
+    return fail(BFS_ERR_INVALID_ARG, "bfs_selector_collect: bad argument");
+  for (int i = 0; i < nroots; ++i)
+    if (roots[i] < 0 || roots[i] >= g->n) return fail(BFS_ERR_INVALID_ARG, "bfs_selector_collect: root outside [0, n)");
+  const size_t n = (size_t)g->n;
+  int32_t* out = nullptr;
+  if (int e = dev_alloc((void**)&out, sizeof(int32_t) * n * 2, "collect outputs")) return e;
+  std::vector<bfs_level_stat> st(kMaxStatLevels);
+  int rows = 0;
+  int rc = BFS_OK;
+  for (int i = 0; i < nroots && !rc; ++i) {
+    // times[v][rep][level]
+    std::vector<std::vector<std::vector<double>>> times(BFS_NUM_VARIANTS);
+    std::vector<bfs_level_stat> first;
+    int nl = -1;
+    for (int v = 0; v < BFS_NUM_VARIANTS && !rc; ++v) {
+      for (int rep = 0; rep < reps + 1 && !rc; ++rep) {  // the first run warms up
+        bfs_opts o{};
+        o.selector = BFS_SELECT_FORCED;
+        o.forced_variant = v;
+        o.stats = st.data();
+        o.max_stat_levels = kMaxStatLevels;
+        int32_t levels = 0;
+        o.nlevels_out = &levels;
+        rc = bfs_run(g, roots[i], out, out + n, &o, stream);
+        if (rc) break;
+        if (nl < 0) {
+          nl = std::min(levels, kMaxStatLevels);
+          first.assign(st.begin(), st.begin() + nl);
+        }
+        if (rep == 0) continue;
+        std::vector<double> t(nl);
+        for (int k = 0; k < nl; ++k) t[k] = (double)st[k].time_ns;
+        times[v].push_back(t);
+      }
+    }
+    if (rc) break;
+    for (int k = 0; k < nl && rows < max_rows; ++k, ++rows) {
+      const bfs_level_stat& s = first[k];
+      const int64_t bins[3] = {s.bin_count[0], s.bin_count[1], s.bin_count[2]};
+      bfs_level_features(g->n, g->nnz, k, s.frontier_count, s.frontier_edges, s.unvisited_count, s.unvisited_edges,
+                         bins, X + (size_t)rows * BFS_MLP_IN);
+      for (int v = 0; v < BFS_NUM_VARIANTS; ++v) {
+        std::vector<double> samples;
+        for (auto& run : times[v]) samples.push_back(run[k]);
+        std::sort(samples.begin(), samples.end());
+        const double med = samples[samples.size() / 2];
+        T[(size_t)rows * BFS_MLP_OUT + v] = (float)std::log2(std::max(med, 1.0) / 1000.0);
+      }
+    }
+  }
+  cudaStreamSynchronize((cudaStream_t)stream);
+  cudaFree(out);
+  if (rc) return rc;
+  *rows_out = rows;
+  return BFS_OK;
+}
+
 int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning* best, void* stream) {
   if (int e = check_graph(g)) return e;
   if (!roots || nroots < 1) return fail(BFS_ERR_INVALID_ARG, "bfs_autotune: need roots");
@@ -632,9 +712,9 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
   // coordinate descent over one knob at a time, two sweeps
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
     const int wd[] = {8, 16, 32, 64};
-    const int cd[] = {256, 1024, 4096};
-    const int pd[] = {8, 16, 32, 64, 128};
-    const int ch[] = {8192, 16384, 65536};
+    const int cd[] = {128, 256, 1024};
+    const int pd[] = {1, 2, 4, 6, 8};
+    const int ch[] = {1024, 4096, 16384};
     const float al[] = {4.0f, 8.0f, 14.0f, 24.0f, 48.0f};
     const float be[] = {8.0f, 16.0f, 24.0f, 48.0f, 96.0f};
     for (int knob = 0; knob < 6 && !rc; ++knob) {

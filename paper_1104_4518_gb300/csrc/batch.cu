@@ -1,6 +1,6 @@
 // Batched BFS: up to 64 roots in one persistent traversal.
 //
-// Every vertex carries three 64-bit words: F_k[v] (bit r set when v is in the
+// Every vertex carries 64-bit words: F_k[v] (bit r set when v is in the
 // frontier of root r at level k), V[v] (bit r set when root r has reached v)
 // and F_{k+1}[v].  One level is the boolean sparse matrix-dense matrix product
 // F_{k+1} = (A (x) F_k) AND NOT V, i.e. the SpMSV of Sec. 3.2 for 64 vectors at
@@ -10,14 +10,20 @@
 // down and masking off the bits already resolved.
 //
 // Two ways to expand a level (identical results):
-//   pull      : every vertex not reached by all roots scans its row (one phase);
-//   top-down  : vertices of the frontier queue OR their bits into F_{k+1} of
-//               their neighbours (first writer enqueues), then every queued
-//               vertex resolves its parents with the same descending scan
-//               (two phases).
+//   pull     : every vertex not yet reached by all roots scans its row (one
+//              phase); short rows lane by lane, long rows by the whole warp;
+//   top-down : the frontier's rows OR their bits into F_{k+1} of unreached
+//              neighbours (the first writer enqueues the neighbour; rows above
+//              kChunkEdges entries are split into chunks, one CTA each), then
+//              every queued vertex resolves its parents with the same
+//              descending scan (two phases).
 // Output rows are root-major: level[r * n + v], parent[r * n + v].
+#include <cooperative_groups.h>
+
 #include "device_common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace bfsint {
 namespace {
@@ -25,6 +31,8 @@ namespace {
 using bfsdev::kFull;
 
 constexpr int kBBlock = 512;
+constexpr int kBWarps = kBBlock / 32;
+constexpr int kShortRow = 32;  // rows up to this length are scanned by one lane
 
 struct BatchParams {
   const int64_t* __restrict__ off;
@@ -39,10 +47,12 @@ struct BatchParams {
   uint64_t* F[3];
   uint64_t* V;
   int32_t* queue[3];
+  int64_t* chunks[2];
   LevelCtr* ctr;
   bfsdev::GridBarrier* bar;
   int* status;
   int32_t* misc;
+  bfs_level_stat* stats;  // per-level statistics when non-null
   unsigned spin_limit;
   long long td_limit;
 };
@@ -58,40 +68,131 @@ __device__ __forceinline__ void write_hits(const BatchParams& p, uint64_t bits, 
   }
 }
 
-// Descending scan of v's row: resolves the parents of the roots in `need`
-// whose frontier (F) contains a neighbour; returns the bits found.
-__device__ __forceinline__ uint64_t resolve_row(const BatchParams& p, const uint64_t* F, int v, uint64_t need,
-                                                int lvl) {
-  const long long b = __ldg(&p.off[v]);
+// One lane scans rows [b, e) of v from the top, four loads at a time, and
+// resolves the roots in `need`; returns the bits found.
+__device__ __forceinline__ uint64_t resolve_lane(const BatchParams& p, const uint64_t* F, int v, long long b,
+                                                 long long e, uint64_t need, int lvl) {
   uint64_t found = 0;
-  for (long long j = __ldg(&p.off[v + 1]) - 1; j >= b && need; --j) {
-    const int u = __ldg(&p.adj[j]);
-    const uint64_t h = F[u] & need;
-    if (h) {
-      write_hits(p, h, v, u, lvl);
-      need &= ~h;
-      found |= h;
+  long long j = e - 1;
+  while (j >= b && need) {
+    int u[4];
+    uint64_t f[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[q] = (j - q >= b) ? __ldg(&p.adj[j - q]) : -1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[q] = u[q] >= 0 ? F[u[q]] : 0ull;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t h = f[q] & need;
+      if (h) {
+        write_hits(p, h, v, u[q], lvl);
+        need &= ~h;
+        found |= h;
+      }
+    }
+    j -= 4;
+  }
+  return found;
+}
+
+// The whole warp scans one row from the top, 32 entries per step; returns the
+// bits found (same value in every lane).
+__device__ __forceinline__ uint64_t resolve_warp(const BatchParams& p, const uint64_t* F, int v, long long b,
+                                                 long long e, uint64_t need, int lvl, int lane) {
+  uint64_t found = 0;
+  for (long long top = e; top > b && need; top -= 32) {
+    const long long j = top - 1 - lane;
+    int u = 0;
+    uint64_t f = 0;
+    if (j >= b) {
+      u = __ldg(&p.adj[j]);
+      f = F[u] & need;
+    }
+    const unsigned lo = __reduce_or_sync(kFull, (unsigned)f);
+    const unsigned hi = __reduce_or_sync(kFull, (unsigned)(f >> 32));
+    uint64_t nb = ((uint64_t)hi << 32) | lo;
+    found |= nb;
+    need &= ~nb;
+    while (nb) {  // each new root takes the lowest lane holding its bit (the highest position)
+      const int r = __ffsll((long long)nb) - 1;
+      nb &= nb - 1;
+      const unsigned who = __ballot_sync(kFull, (f >> r) & 1ull);
+      const int src = __ffs(who) - 1;
+      const int pu = __shfl_sync(kFull, u, src);
+      if (lane == 0) {
+        const long long o = (long long)r * p.n + v;
+        p.level[o] = lvl;
+        p.parent[o] = pu;
+      }
     }
   }
   return found;
 }
 
-__device__ __forceinline__ void enqueue_warp(const BatchParams& p, int knext, int v, bool pred) {
+__device__ __forceinline__ void push_chunks(const BatchParams& p, int knext, int v, long long deg) {
+  const unsigned nch = (unsigned)((deg + kChunkEdges - 1) / kChunkEdges);
+  const unsigned pos = atomicAdd(&p.ctr[knext % kCtrRing].chunks, nch);
+  int64_t* dst = p.chunks[knext & 1];
+  for (unsigned c = 0; c < nch; ++c) dst[pos + c] = ((int64_t)v << 32) | (int64_t)c;
+}
+
+// Warp-aggregated append of v (when pred) to the queue of level knext.
+__device__ __forceinline__ void enqueue_warp(const BatchParams& p, int knext, int v, bool pred, long long deg) {
   const unsigned m = __ballot_sync(kFull, pred);
   if (!m) return;
   const int lane = threadIdx.x & 31;
   unsigned base = 0;
   if (lane == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)__popc(m));
   base = __shfl_sync(kFull, base, 0);
-  if (pred) p.queue[knext % 3][base + __popc(m & bfsdev::lanemask_lt())] = v;
+  if (pred) {
+    p.queue[knext % 3][base + __popc(m & bfsdev::lanemask_lt())] = v;
+    if (deg > kChunkEdges) push_chunks(p, knext, v, deg);
+  }
 }
 
-__global__ void __launch_bounds__(kBBlock) batch_kernel(BatchParams p) {
-  const int tid = threadIdx.x;
+// Resolves the parents of 32 vertices (one per lane, need = roots to find)
+// against frontier F; lanes with short rows scan alone, long rows get the warp.
+__device__ __forceinline__ uint64_t resolve_group(const BatchParams& p, const uint64_t* F, int v, long long b,
+                                                  long long e, uint64_t need, int lvl, int lane) {
+  uint64_t found = 0;
+  const bool longrow = need && (e - b) > kShortRow;
+  if (need && !longrow) found = resolve_lane(p, F, v, b, e, need, lvl);
+  unsigned lm = __ballot_sync(kFull, longrow);
+  while (lm) {
+    const int l = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const int lv = __shfl_sync(kFull, v, l);
+    const long long lb = __shfl_sync(kFull, b, l), le = __shfl_sync(kFull, e, l);
+    const uint64_t ln = __shfl_sync(kFull, need, l);
+    const uint64_t fw = resolve_warp(p, F, lv, lb, le, ln, lvl, lane);
+    if (lane == l) found = fw;
+  }
+  return found;
+}
+
+// Top-down discover of edge (u -> w) with frontier bits f.
+__device__ __forceinline__ void discover(const BatchParams& p, uint64_t* Fn, int knext, uint64_t f, int w) {
+  const uint64_t nb = f & ~p.V[w];
+  if (!nb || (Fn[w] & nb) == nb) return;
+  const unsigned long long old = atomicOr((unsigned long long*)&Fn[w], (unsigned long long)nb);
+  if (old == 0) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)g.size());
+    base = g.shfl(base, 0);
+    p.queue[knext % 3][base + g.thread_rank()] = w;
+  }
+}
+
+__global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
+  const int tid = threadIdx.x, lane = tid & 31;
   unsigned epoch = 0;
   if (tid == 0) epoch = bfsdev::ld_acquire_u32(&p.bar->epoch);
+  const long long G = gridDim.x;
   const long long gtid = (long long)blockIdx.x * kBBlock + tid;
-  const long long gthreads = (long long)gridDim.x * kBBlock;
+  const long long gthreads = G * kBBlock;
+  const long long gwarps = G * kBWarps;
+  const long long gwarp = blockIdx.x + (long long)(tid >> 5) * G;  // round-robin over CTAs
   const unsigned nblocks = gridDim.x;
 
   // init: outputs to -1, bitsets to 0, counters to 0
@@ -122,14 +223,19 @@ __global__ void __launch_bounds__(kBBlock) batch_kernel(BatchParams p) {
     if (old == 0) {
       const unsigned pos = atomicAdd(&p.ctr[0].count, 1u);
       p.queue[0][pos] = s;
+      const long long deg = __ldg(&p.off[s + 1]) - __ldg(&p.off[s]);
+      if (deg > kChunkEdges) push_chunks(p, 0, s, deg);
     }
   }
   if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
 
   int k = 0;
+  uint64_t t_prev = 0;
+  if (p.stats && blockIdx.x == 0 && tid == 0) t_prev = bfsdev::global_timer_ns();
   for (;; ++k) {
     const unsigned count = __ldcg(&p.ctr[k % kCtrRing].count);
     if (count == 0) break;
+    const unsigned nchunks = __ldcg(&p.ctr[k % kCtrRing].chunks);
     const uint64_t* Fc = p.F[k % 3];
     uint64_t* Fn = p.F[(k + 1) % 3];
     const int32_t* Q = p.queue[k % 3];
@@ -147,51 +253,80 @@ __global__ void __launch_bounds__(kBBlock) batch_kernel(BatchParams p) {
       }
     }
 
-    if ((long long)count <= p.td_limit) {
-      // top-down discover: OR frontier bits into unreached neighbours
-      for (long long i = gtid; i < count; i += gthreads) {
-        const int u = Q[i];
+    const bool topdown = (long long)count <= p.td_limit;
+    if (topdown) {
+      // top-down discover: chunks of long rows (one CTA each), then one warp per short row
+      const int64_t* items = p.chunks[k & 1];
+      for (long long ci = blockIdx.x; ci < nchunks; ci += G) {
+        const int64_t it = items[ci];
+        const int u = (int)(it >> 32);
+        const long long rb = __ldg(&p.off[u]) + (it & 0xffffffffll) * kChunkEdges;
+        const long long re = min(rb + (long long)kChunkEdges, (long long)__ldg(&p.off[u + 1]));
         const uint64_t f = Fc[u];
+        for (long long j = rb + tid; j < re; j += kBBlock) discover(p, Fn, knext, f, __ldg(&p.adj[j]));
+      }
+      for (long long i = gwarp; i < count; i += gwarps) {
+        const int u = Q[i];
         const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
-        for (long long j = b; j < e; ++j) {
-          const int w = __ldg(&p.adj[j]);
-          const uint64_t nb = f & ~p.V[w];
-          if (!nb || (Fn[w] & nb) == nb) continue;
-          const unsigned long long old = atomicOr((unsigned long long*)&Fn[w], (unsigned long long)nb);
-          if (old == 0) {
-            const unsigned pos = atomicAdd(&p.ctr[knext % kCtrRing].count, 1u);
-            p.queue[knext % 3][pos] = w;
-          }
-        }
+        if (e - b > kChunkEdges) continue;
+        const uint64_t f = Fc[u];
+        for (long long j = b + lane; j < e; j += 32) discover(p, Fn, knext, f, __ldg(&p.adj[j]));
       }
       if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
-      // resolve parents of the newly reached (vertex, root) pairs
+      // resolve parents of the newly reached (vertex, root) pairs, 32 queue entries per warp
       const unsigned ncount = __ldcg(&p.ctr[knext % kCtrRing].count);
       const int32_t* NQ = p.queue[knext % 3];
-      for (long long i = gtid; i < ncount; i += gthreads) {
-        const int w = NQ[i];
-        const uint64_t need = Fn[w];
-        resolve_row(p, Fc, w, need, knext);
-        p.V[w] |= need;
+      for (long long base = gwarp * 32; base < ncount; base += gwarps * 32) {
+        const long long i = base + lane;
+        int w = 0;
+        uint64_t need = 0;
+        long long b = 0, e = 0;
+        if (i < ncount) {
+          w = NQ[i];
+          need = Fn[w];
+          b = __ldg(&p.off[w]);
+          e = __ldg(&p.off[w + 1]);
+        }
+        resolve_group(p, Fc, w, b, e, need, knext, lane);
+        if (i < ncount) {
+          p.V[w] |= need;
+          if (e - b > kChunkEdges) push_chunks(p, knext, w, e - b);
+        }
       }
     } else {
-      // pull: every vertex with unreached roots scans its row
-      const long long nw = ((long long)p.n + 31) / 32 * 32;
-      for (long long v0 = gtid; v0 < nw; v0 += gthreads) {
+      // pull: every vertex with unreached roots scans its row, 32 vertices per warp
+      const long long nw = ((long long)p.n + 31) / 32;
+      for (long long ww = gwarp; ww < nw; ww += gwarps) {
+        const long long v0 = ww * 32 + lane;
         const int v = (int)v0;
-        uint64_t found = 0;
+        uint64_t need = 0;
+        long long b = 0, e = 0;
         if (v0 < p.n) {
-          const uint64_t need = ~p.V[v] & p.mask;
-          if (need) found = resolve_row(p, Fc, v, need, knext);
-          if (found) {
-            Fn[v] = found;
-            p.V[v] |= found;
+          need = ~p.V[v] & p.mask;
+          if (need) {
+            b = __ldg(&p.off[v]);
+            e = __ldg(&p.off[v + 1]);
+            if (e == b) need = 0;
           }
         }
-        enqueue_warp(p, knext, v, found != 0);
+        const uint64_t found = resolve_group(p, Fc, v, b, e, need, knext, lane);
+        if (found) {
+          Fn[v] = found;
+          p.V[v] |= found;
+        }
+        enqueue_warp(p, knext, v, found != 0, e - b);
       }
     }
     if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+    if (p.stats && blockIdx.x == 0 && tid == 0 && k < kMaxStatLevels) {
+      const uint64_t t = bfsdev::global_timer_ns();
+      bfs_level_stat st{};
+      st.frontier_count = count;
+      st.time_ns = (int64_t)(t - t_prev);
+      st.variant = topdown ? BFS_VARIANT_TD_WARP : BFS_VARIANT_PULL;
+      p.stats[k] = st;
+      t_prev = t;
+    }
   }
   if (gtid == 0) p.misc[1] = k;
 }
@@ -221,10 +356,13 @@ int launch_batch(const BatchRequest& r, cudaStream_t s) {
     p.queue[i] = w->queue[i];
   }
   p.V = w->bvis;
+  p.chunks[0] = w->chunks[0];
+  p.chunks[1] = w->chunks[1];
   p.ctr = w->ctr;
   p.bar = reinterpret_cast<bfsdev::GridBarrier*>(w->barrier);
   p.status = w->status;
   p.misc = w->misc;
+  p.stats = r.want_stats ? w->stats : nullptr;
   p.spin_limit = r.spin_limit ? r.spin_limit : (1u << 25);
   p.td_limit = t.batch_topdown_limit;
   int per_sm = 0;

@@ -332,6 +332,18 @@ __global__ void shift_kernel(int64_t* off, int32_t* adj, long long n_part, long 
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nnz_part; j += stride) adj[j] += id_shift;
 }
 
+__global__ void dead_bits_kernel(const int64_t* __restrict__ off, int32_t n, long long nwords, uint32_t* out) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const long long stride = (long long)gridDim.x * blockDim.x / 32;
+  const int lane = threadIdx.x & 31;
+  for (long long w = gw; w < nwords; w += stride) {
+    const long long v = w * 32 + lane;
+    const bool dead = v >= n || off[v + 1] == off[v];
+    const unsigned m = __ballot_sync(kFull, dead);
+    if (lane == 0) out[w] = m;
+  }
+}
+
 int bits_for(int32_t n) {
   int b = 1;
   while (b < 31 && ((int64_t)1 << b) < (int64_t)n) ++b;
@@ -448,6 +460,14 @@ int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, 
   *d_off_out = off;
   *d_adj_out = adj;
   *nnz_out = nnz;
+  return BFS_OK;
+}
+
+int compute_dead_bits(const int64_t* d_off, int32_t n, uint32_t* d_dead, cudaStream_t s) {
+  DeviceInfo di;
+  if (int e = current_device_info(&di)) return e;
+  dead_bits_kernel<<<di.sm_count * 4, 256, 0, s>>>(d_off, n, ((long long)n + 31) / 32, d_dead);
+  BFS_CUDA_TRY(cudaGetLastError());
   return BFS_OK;
 }
 

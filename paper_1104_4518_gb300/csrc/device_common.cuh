@@ -53,6 +53,9 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 // error) the CTA records BFS_ERR_TIMEOUT in *status and the barrier returns
 // false, so that the kernel can return instead of hanging.  `epoch` is the
 // CTA's copy of the release counter (read once at kernel start).
+// Ordering: __syncthreads + a gpu-scope fence by thread 0 publish the CTA's
+// writes before its arrival; the acquire load that sees the new epoch, then
+// __syncthreads, order the CTA's later reads after every CTA's writes.
 __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned nblocks, unsigned& epoch,
                                              unsigned spin_limit, int* status) {
   __shared__ int s_ok;
@@ -72,12 +75,10 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned nblocks,
           ok = 0;
           break;
         }
-        __nanosleep(40);
+        __nanosleep(32);
       }
     }
     if (!ok) atomicCAS(status, 0, (int)BFS_ERR_TIMEOUT);
-    if (ok && ld_relaxed_i32(status) != 0) ok = 0;
-    __threadfence();
     epoch = target;
     s_ok = ok;
   }

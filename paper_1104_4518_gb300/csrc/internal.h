@@ -47,7 +47,7 @@ struct __align__(64) LevelCtr {
 };
 
 // Edges per chunk item of a high-degree top-down vertex (one CTA pass).
-constexpr int kChunkEdges = 4096;
+constexpr int kChunkEdges = 1024;
 
 // Device stats record written by the level loop (mirrors bfs_level_stat).
 static_assert(sizeof(bfs_level_stat) == 72, "bfs_level_stat layout");
@@ -95,6 +95,7 @@ struct bfs_graph {
   int64_t nnz = 0;
   int64_t* d_off = nullptr;
   int32_t* d_adj = nullptr;
+  uint32_t* d_dead = nullptr;  // bitmap of vertices without edges (tail bits set)
   int32_t parts = 1;
   std::vector<int64_t> part_base;  // parts + 1 entries (union graphs)
   int64_t* d_part_base = nullptr;
@@ -121,6 +122,8 @@ bfs_tuning effective_tuning(const bfs_graph* g);
 // CSR construction from an edge list (device pointers).  Allocates d_off/d_adj.
 int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n,
                          cudaStream_t s, int64_t** d_off, int32_t** d_adj, int64_t* nnz);
+// Bitmap of the vertices without edges (bits beyond n set), one word per 32 vertices.
+int compute_dead_bits(const int64_t* d_off, int32_t n, uint32_t* d_dead, cudaStream_t s);
 // Adds off_shift to n_part offsets and id_shift to nnz_part ids (union building).
 int union_shift(int64_t* off, int32_t* adj, int64_t n_part, int64_t nnz_part, int64_t off_shift, int32_t id_shift,
                 cudaStream_t s);

@@ -20,12 +20,18 @@
 //   top-down (thread / warp / degree-binned): for u in f_k and every neighbour w
 //     not yet reached, atomicMax(parent[w], u) -- every frontier neighbour of w
 //     contributes, so parent[w] ends as the largest-id one -- and the first
-//     atomicOr on nxt claims w (level, queue, counters).  Vertices above the
-//     chunk degree are split into grid-wide chunk items of kChunkEdges edges.
+//     atomicOr on nxt claims w (level, queue, counters).  Frontier entries are
+//     dealt round-robin over the CTAs so that small frontiers use every SM, and
+//     vertices above the chunk degree are split into grid-wide chunk items of
+//     kChunkEdges edges, one CTA each.
 //   pull: for every vertex v not yet reached, scan its sorted row from the
 //     largest id down; the first neighbour in f_k is the max-id parent.  One
 //     warp owns 32 consecutive vertices (one bitmap word), so nxt / vis words
-//     are written without atomics and the next queue is compacted by ballot.
+//     are written without atomics.  Each lane first probes the top entries of
+//     its own row; rows still open are then scanned by the whole warp, 32
+//     entries per step, packed across rows by a warp prefix sum (per-row early
+//     exit is kept).  Vertices without edges are marked visited at init, so
+//     pull levels never touch them.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -44,9 +50,34 @@ using bfsdev::kFull;
 constexpr int kBlock = 512;
 constexpr int kWarps = kBlock / 32;
 
+#ifdef BFS_PHASE_TIMING
+// Diagnostic build only: global-timer stamps of the first 4096 levels.
+// [0] CTA 0 at level start, [1] after selection, [2] after recycling,
+// [3] after expansion, [4] after counter flush, [5] latest barrier arrival
+// of any CTA, [6] CTA 0 after the barrier.
+__device__ unsigned long long g_phase_ts[4096][8];
+#define PHASE_TS(k, slot)                                                             \
+  do {                                                                                \
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (k) < 4096) g_phase_ts[k][slot] = bfsdev::global_timer_ns(); \
+  } while (0)
+#define PHASE_ARRIVAL(k)                                                              \
+  do {                                                                                \
+    __syncthreads();                                                                  \
+    if (threadIdx.x == 0 && (k) < 4096) atomicMax(&g_phase_ts[k][5], (unsigned long long)bfsdev::global_timer_ns()); \
+  } while (0)
+#else
+#define PHASE_TS(k, slot) \
+  do {                    \
+  } while (0)
+#define PHASE_ARRIVAL(k) \
+  do {                   \
+  } while (0)
+#endif
+
 struct LoopParams {
   const int64_t* __restrict__ off;
   const int32_t* __restrict__ adj;
+  const uint32_t* __restrict__ dead;  // vertices without edges (and the tail), or null
   int32_t n;
   int32_t nwords;
   long long nnz;
@@ -100,14 +131,13 @@ __device__ __forceinline__ void push_chunks(const LoopParams& p, int knext, int 
 }
 
 // Bookkeeping of a vertex claimed for level knext (the caller already set nxt).
-__device__ __forceinline__ void claim_topdown(const LoopParams& p, int knext, int w, Acc& acc) {
+__device__ __forceinline__ void claim_topdown(const LoopParams& p, int knext, int w, long long deg, Acc& acc) {
   p.level[w] = knext;
   cg::coalesced_group g = cg::coalesced_threads();
   unsigned base = 0;
   if (g.thread_rank() == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)g.size());
   base = g.shfl(base, 0);
   p.queue[knext % 3][base + g.thread_rank()] = w;
-  const long long deg = __ldg(&p.off[w + 1]) - __ldg(&p.off[w]);
   acc_vertex(acc, deg);
   if (deg > p.chunk_deg) push_chunks(p, knext, w, deg);
 }
@@ -117,50 +147,69 @@ __device__ __forceinline__ void td_visit(const LoopParams& p, const uint32_t* cu
                                          int u, int w, Acc& acc) {
   const int ww = w >> 5;
   const uint32_t m = 1u << (w & 31);
-  const uint32_t seen = p.vis[ww] | cur[ww];
-  if (seen & m) return;
+  const uint32_t vw = p.vis[ww], cw = cur[ww], nw = nxt[ww];  // independent loads, one round trip
+  if ((vw | cw) & m) return;
   atomicMax(&p.parent[w], u);
-  if (nxt[ww] & m) return;
+  if (nw & m) return;
+  const long long wb = __ldg(&p.off[w]), we = __ldg(&p.off[w + 1]);  // speculative: the claim needs the degree
   const uint32_t old = atomicOr(&nxt[ww], m);
   if (old & m) return;
-  claim_topdown(p, k + 1, w, acc);
+  claim_topdown(p, k + 1, w, we - wb, acc);
 }
 
-// Descending scan of one row for the first neighbour whose bit is set in `bm`
-// (= the largest-id neighbour in that set, rows being sorted ascending).
-__device__ __forceinline__ int scan_desc_thread(const int32_t* __restrict__ adj, long long b, long long e,
-                                                const uint32_t* bm) {
-  long long j = e - 1;
-  for (; j - 3 >= b; j -= 4) {
-    const int u0 = __ldg(&adj[j]), u1 = __ldg(&adj[j - 1]), u2 = __ldg(&adj[j - 2]), u3 = __ldg(&adj[j - 3]);
-    const uint32_t w0 = bm[u0 >> 5], w1 = bm[u1 >> 5], w2 = bm[u2 >> 5], w3 = bm[u3 >> 5];
-    if ((w0 >> (u0 & 31)) & 1u) return u0;
-    if ((w1 >> (u1 & 31)) & 1u) return u1;
-    if ((w2 >> (u2 & 31)) & 1u) return u2;
-    if ((w3 >> (u3 & 31)) & 1u) return u3;
-  }
-  for (; j >= b; --j) {
-    const int u = __ldg(&adj[j]);
-    if ((bm[u >> 5] >> (u & 31)) & 1u) return u;
-  }
-  return -1;
-}
-
-// Same scan done by a whole warp, 32 entries per step (all lanes call it).
-__device__ __forceinline__ int scan_desc_warp(const int32_t* __restrict__ adj, long long b, long long e,
-                                              const uint32_t* bm, int lane) {
-  for (long long top = e; top > b; top -= 32) {
-    const long long j = top - 1 - lane;
+// Warp-cooperative descending scan of the rows still open in a warp: lane r
+// owns row r with entries [b, t) not yet examined (t exclusive, scanned from
+// t-1 down).  Every step the open rows' next entries are packed onto the 32
+// lanes by a prefix sum (at most 32 per row), each lane tests one entry
+// against the bitmap `bm`, and a row whose segment has a hit takes the hit of
+// its lowest lane (its highest position, i.e. its largest id) and closes.
+// All lanes call it; returns the row's hit or -1.
+__device__ __forceinline__ int scan_desc_coop(const int32_t* __restrict__ adj, const uint32_t* bm, long long b,
+                                              long long t, bool open, int hit, int lane) {
+  unsigned pm = __ballot_sync(kFull, open);
+  while (pm) {
+    const int rc = open ? (int)min(t - b, 32ll) : 0;
+    int incl = rc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - rc;
+    const int total = __shfl_sync(kFull, incl, 31);
+    // owner row of this lane's slot: the last row whose prefix is <= lane
+    int r = 0;
+#pragma unroll
+    for (int st = 16; st >= 1; st >>= 1) {
+      const int c = r + st;
+      const int ec = __shfl_sync(kFull, excl, c & 31);
+      if (c < 32 && ec <= lane) r = c;
+    }
+    const long long tr = __shfl_sync(kFull, t, r);
+    const int er = __shfl_sync(kFull, excl, r);
     int u = 0;
     bool h = false;
-    if (j >= b) {
-      u = __ldg(&adj[j]);
+    if (lane < total) {
+      u = __ldg(&adj[tr - 1 - (lane - er)]);
       h = (bm[u >> 5] >> (u & 31)) & 1u;
     }
     const unsigned hm = __ballot_sync(kFull, h);
-    if (hm) return __shfl_sync(kFull, u, __ffs(hm) - 1);
+    const int cons = max(0, min(rc, 32 - excl));
+    const unsigned seg = cons > 0 ? ((cons == 32 ? kFull : ((1u << cons) - 1u)) << excl) : 0u;
+    const unsigned mine = hm & seg;
+    const int hv = __shfl_sync(kFull, u, mine ? __ffs(mine) - 1 : 0);
+    if (open) {
+      if (mine) {
+        hit = hv;
+        open = false;
+      } else {
+        t -= cons;
+        if (t <= b) open = false;
+      }
+    }
+    pm = __ballot_sync(kFull, open);
   }
-  return -1;
+  return hit;
 }
 
 // 64-bit warp sum.
@@ -230,6 +279,7 @@ struct Smem {
   int tu[kBlock];
   long long tb[kBlock];
   int tpref[kBlock + 1];
+  int qbuf[kWarps][64];
   float x[12];
   float h1[64];
   float h2[64];
@@ -257,9 +307,11 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
     for (long long j = b + tid; j < e; j += kBlock) td_visit(p, cur, nxt, k, v, __ldg(&p.adj[j]), acc);
   }
 
-  const long long gthreads = (long long)gridDim.x * kBlock;
+  // frontier entry i goes to CTA i % G, so that small frontiers spread over every SM
+  const long long G = gridDim.x;
+  const long long gthreads = G * kBlock;
   if (variant == BFS_VARIANT_TD_THREAD) {
-    for (long long i = (long long)blockIdx.x * kBlock + tid; i < count; i += gthreads) {
+    for (long long i = blockIdx.x + (long long)tid * G; i < count; i += gthreads) {
       const int u = Q[i];
       atomicOr(&p.vis[u >> 5], 1u << (u & 31));
       const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
@@ -268,7 +320,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
     }
   } else if (variant == BFS_VARIANT_TD_WARP) {
     const long long gwarps = gthreads / 32;
-    for (long long i = ((long long)blockIdx.x * kBlock + tid) / 32; i < count; i += gwarps) {
+    for (long long i = blockIdx.x + (long long)(tid >> 5) * G; i < count; i += gwarps) {
       const int u = Q[i];
       if (lane == 0) atomicOr(&p.vis[u >> 5], 1u << (u & 31));
       const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
@@ -276,8 +328,8 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
       for (long long j = b + lane; j < e; j += 32) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc);
     }
   } else {  // BFS_VARIANT_TD_BINNED
-    for (long long tile = (long long)blockIdx.x * kBlock; tile < count; tile += gthreads) {
-      const long long i = tile + tid;
+    for (long long tile = 0; tile < count; tile += gthreads) {
+      const long long i = tile + blockIdx.x + (long long)tid * G;
       int u = -1;
       long long b = 0, e = 0;
       if (i < count) {
@@ -346,13 +398,38 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
 }
 
 // ---------------- pull phase ----------------
-__device__ void pull_phase(const LoopParams& p, int k, Acc& acc) {
+// Appends a warp's claimed vertices through a 64-entry shared buffer: one
+// queue atomic per 32 vertices instead of one per bitmap word.
+__device__ __forceinline__ void pull_enqueue(const LoopParams& p, int knext, int* qbuf, int& nbuf, bool claimed,
+                                             int v, int lane, bool flush_all) {
+  const unsigned hm = __ballot_sync(kFull, claimed);
+  if (claimed) qbuf[nbuf + __popc(hm & bfsdev::lanemask_lt())] = v;
+  nbuf += __popc(hm);
+  __syncwarp();
+  while (nbuf >= 32 || (flush_all && nbuf > 0)) {
+    const int take = min(nbuf, 32);
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)take);
+    base = __shfl_sync(kFull, base, 0);
+    int moved = 0;
+    if (lane < take) p.queue[knext % 3][base + lane] = qbuf[lane];
+    if (lane + 32 < nbuf) moved = qbuf[lane + 32];
+    __syncwarp();
+    if (lane + 32 < nbuf) qbuf[lane] = moved;
+    __syncwarp();
+    nbuf -= take;
+  }
+}
+
+__device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
   const uint32_t* cur = p.bits[k % 3];
   uint32_t* nxt = p.bits[(k + 1) % 3];
-  int32_t* NQ = p.queue[(k + 1) % 3];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long gwarps = (long long)gridDim.x * kWarps;
   const int knext = k + 1;
+  const int probe = p.pull_thread_deg;
+  int* qbuf = sm.qbuf[wid];
+  int nbuf = 0;
   for (long long ww = ((long long)blockIdx.x * kBlock + threadIdx.x) / 32; ww < p.nwords; ww += gwarps) {
     const uint32_t vw = p.vis[ww];
     const uint32_t visw = vw | cur[ww];
@@ -367,35 +444,40 @@ __device__ void pull_phase(const LoopParams& p, int k, Acc& acc) {
       b = __ldg(&p.off[v]);
       e = __ldg(&p.off[v + 1]);
     }
-    const long long deg = e - b;
+    // probe: each lane tests the top entries of its own row (loads issued together)
     int hit = -1;
-    const bool longrow = active && deg > p.pull_thread_deg;
-    if (active && !longrow) hit = scan_desc_thread(p.adj, b, e, cur);
-    unsigned lm = __ballot_sync(kFull, longrow);
-    while (lm) {
-      const int l = __ffs(lm) - 1;
-      lm &= lm - 1;
-      const long long lb = __shfl_sync(kFull, b, l), le = __shfl_sync(kFull, e, l);
-      const int h = scan_desc_warp(p.adj, lb, le, cur, lane);
-      if (lane == l) hit = h;
+    long long t = e;
+    if (active) {
+      const int P = (int)min((long long)probe, e - b);
+      int u[8];
+      uint32_t wv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < P) u[q] = __ldg(&p.adj[e - 1 - q]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < P) wv[q] = cur[u[q] >> 5];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < P && hit < 0 && ((wv[q] >> (u[q] & 31)) & 1u)) hit = u[q];
+      t = e - P;
     }
+    hit = scan_desc_coop(p.adj, cur, b, t, active && hit < 0 && t > b, hit, lane);
     const unsigned hits = __ballot_sync(kFull, hit >= 0);
     if (lane == 0) {
       if (hits) nxt[ww] = hits;
-      p.vis[ww] = visw | hits;
+      if ((visw | hits) != vw) p.vis[ww] = visw | hits;
     }
-    if (!hits) continue;
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)__popc(hits));
-    base = __shfl_sync(kFull, base, 0);
     if (hit >= 0) {
       p.parent[v] = hit;
       p.level[v] = knext;
-      NQ[base + __popc(hits & bfsdev::lanemask_lt())] = v;
+      const long long deg = e - b;
       acc_vertex(acc, deg);
       if (deg > p.chunk_deg) push_chunks(p, knext, v, deg);
     }
+    if (hits) pull_enqueue(p, knext, qbuf, nbuf, hit >= 0, v, lane, false);
   }
+  pull_enqueue(p, knext, qbuf, nbuf, false, 0, lane, true);
 }
 
 __device__ __forceinline__ int heuristic_variant(const LoopParams& p, int prev_variant, long long count,
@@ -404,12 +486,10 @@ __device__ __forceinline__ int heuristic_variant(const LoopParams& p, int prev_v
   bool pull;
   if (prev_variant == BFS_VARIANT_PULL) pull = (float)count * p.beta >= (float)p.n;
   else pull = (float)edges * p.alpha > (float)unvisited_edges;
-  if (pull) return BFS_VARIANT_PULL;
-  if (bins[1] + bins[2] == 0) return BFS_VARIANT_TD_THREAD;
-  return BFS_VARIANT_TD_BINNED;
+  return pull ? BFS_VARIANT_PULL : BFS_VARIANT_TD_BINNED;
 }
 
-__global__ void __launch_bounds__(kBlock) level_loop_kernel(LoopParams p) {
+__global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   __shared__ Smem sm;
   extern __shared__ float s_mlp[];  // BFS_MLP_PARAMS floats when the learned selector is on
   const int tid = threadIdx.x;
@@ -427,39 +507,63 @@ __global__ void __launch_bounds__(kBlock) level_loop_kernel(LoopParams p) {
   const long long gthreads = (long long)gridDim.x * kBlock;
   const unsigned nblocks = gridDim.x;
 
-  // ---- init: outputs to -1, bitmaps cleared (tail bits of vis set), counters zeroed
-  for (long long v = gtid; v < p.n; v += gthreads) {
-    p.level[v] = -1;
-    p.parent[v] = -1;
+  // ---- init: outputs to -1, bitmaps cleared, counters zeroed.  One warp per
+  // bitmap word.  Vertices without edges (and the tail beyond n) start as
+  // visited, since no traversal can reach them.  A single source is seeded in
+  // the same phase; several sources (ragged runs) get a seeding phase of their own.
+  const bool single = p.nsources == 1;
+  const int s0 = p.src0;
+  const long long nv32 = (long long)p.nwords * 32;
+  for (long long v = gtid; v < nv32; v += gthreads) {
+    bool dead = true;
+    if (v < p.n) {
+      const bool src = single && v == s0;
+      p.level[v] = src ? 0 : -1;
+      p.parent[v] = src ? s0 : -1;
+      dead = src || (p.dead == nullptr && __ldg(&p.off[v + 1]) == __ldg(&p.off[v]));
+    }
+    unsigned dm = __ballot_sync(kFull, dead);
+    if ((tid & 31) == 0) {
+      const long long w = v >> 5;
+      if (p.dead != nullptr) dm |= __ldg(&p.dead[w]);
+      p.bits[0][w] = (single && w == (s0 >> 5)) ? (1u << (s0 & 31)) : 0u;
+      p.bits[1][w] = 0;
+      p.bits[2][w] = 0;
+      p.vis[w] = dm;
+    }
   }
-  const uint32_t tail = (p.n & 31) ? ~((1u << (p.n & 31)) - 1u) : 0u;
-  for (long long w = gtid; w < p.nwords; w += gthreads) {
-    p.bits[0][w] = 0;
-    p.bits[1][w] = 0;
-    p.bits[2][w] = 0;
-    p.vis[w] = (w == p.nwords - 1) ? tail : 0u;
+  if (blockIdx.x == 0) {
+    if (tid < kCtrRing * (int)(sizeof(LevelCtr) / 8)) reinterpret_cast<unsigned long long*>(p.ctr)[tid] = 0ull;
+    __syncthreads();
+    if (single && tid == 0) {
+      p.queue[0][0] = s0;
+      const long long deg = __ldg(&p.off[s0 + 1]) - __ldg(&p.off[s0]);
+      p.ctr[0].count = 1;
+      p.ctr[0].edges = (unsigned long long)deg;
+      p.ctr[0].bins[deg <= 32 ? 0 : (deg <= 1024 ? 1 : 2)] = 1;
+      if (deg > p.chunk_deg) push_chunks(p, 0, s0, deg);
+    }
   }
-  if (blockIdx.x == 0 && tid < kCtrRing * (int)(sizeof(LevelCtr) / 8))
-    reinterpret_cast<unsigned long long*>(p.ctr)[tid] = 0ull;
   if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
 
-  // ---- seed level 0 with the sources (block 0)
-  if (blockIdx.x == 0) {
-    Acc acc;
-    for (int i = tid; i < p.nsources; i += kBlock) {
-      const int s = p.nsources == 1 ? p.src0 : p.sources[i];
-      p.level[s] = 0;
-      p.parent[s] = s;
-      atomicOr(&p.bits[0][s >> 5], 1u << (s & 31));
-      p.queue[0][i] = s;
-      const long long deg = __ldg(&p.off[s + 1]) - __ldg(&p.off[s]);
-      acc_vertex(acc, deg);
-      if (deg > p.chunk_deg) push_chunks(p, 0, s, deg);
+  if (!single) {  // seed level 0 with the sources (block 0)
+    if (blockIdx.x == 0) {
+      Acc acc;
+      for (int i = tid; i < p.nsources; i += kBlock) {
+        const int s = p.sources[i];
+        p.level[s] = 0;
+        p.parent[s] = s;
+        atomicOr(&p.bits[0][s >> 5], 1u << (s & 31));
+        p.queue[0][i] = s;
+        const long long deg = __ldg(&p.off[s + 1]) - __ldg(&p.off[s]);
+        acc_vertex(acc, deg);
+        if (deg > p.chunk_deg) push_chunks(p, 0, s, deg);
+      }
+      if (tid == 0) p.ctr[0].count = (unsigned)p.nsources;
+      flush_acc(p, 0, acc, sm.acc);
     }
-    if (tid == 0) p.ctr[0].count = (unsigned)p.nsources;
-    flush_acc(p, 0, acc, sm.acc);
+    if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
   }
-  if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
 
   // ---- level loop
   long long cum_count = 0, cum_edges = 0;
@@ -469,6 +573,7 @@ __global__ void __launch_bounds__(kBlock) level_loop_kernel(LoopParams p) {
   int k = 0;
   Acc acc;
   for (;; ++k) {
+    PHASE_TS(k, 0);
     const LevelCtr* c = &p.ctr[k % kCtrRing];
     const unsigned count = __ldcg(&c->count);
     if (count == 0) break;
@@ -509,6 +614,7 @@ __global__ void __launch_bounds__(kBlock) level_loop_kernel(LoopParams p) {
     }
     if (variant < 0 || variant >= BFS_NUM_VARIANTS) variant = BFS_VARIANT_TD_BINNED;
 
+    PHASE_TS(k, 1);
     // recycle: counters of level k+4, bitmap of level k-1
     if (blockIdx.x == 0 && tid < (int)(sizeof(LevelCtr) / 8))
       reinterpret_cast<unsigned long long*>(&p.ctr[(k + 4) % kCtrRing])[tid] = 0ull;
@@ -523,10 +629,15 @@ __global__ void __launch_bounds__(kBlock) level_loop_kernel(LoopParams p) {
       }
     }
 
-    if (variant == BFS_VARIANT_PULL) pull_phase(p, k, acc);
+    PHASE_TS(k, 2);
+    if (variant == BFS_VARIANT_PULL) pull_phase(p, k, sm, acc);
     else topdown_phase(p, k, variant, count, nchunks, sm, acc);
+    PHASE_TS(k, 3);
     flush_acc(p, k + 1, acc, sm.acc);
+    PHASE_TS(k, 4);
+    PHASE_ARRIVAL(k);
     if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+    PHASE_TS(k, 6);
 
     if (p.want_stats && blockIdx.x == 0 && tid == 0 && k < kMaxStatLevels) {
       const uint64_t t = bfsdev::global_timer_ns();
@@ -568,6 +679,17 @@ __global__ void __launch_bounds__(kBlock) level_loop_kernel(LoopParams p) {
 
 }  // namespace
 
+#ifdef BFS_PHASE_TIMING
+extern "C" __attribute__((visibility("default"))) int bfs_debug_phase_times(unsigned long long* host, int levels) {
+  if (levels > 4096) levels = 4096;
+  cudaDeviceSynchronize();
+  if (cudaMemcpyFromSymbol(host, g_phase_ts, sizeof(unsigned long long) * 8 * levels) != cudaSuccess) return 1;
+  static unsigned long long zero[4096][8];
+  cudaMemcpyToSymbol(g_phase_ts, zero, sizeof(zero));
+  return 0;
+}
+#endif
+
 int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   bfs_graph* g = r.g;
   Workspace* w = r.w;
@@ -594,6 +716,7 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   LoopParams p{};
   p.off = g->d_off;
   p.adj = g->d_adj;
+  p.dead = g->d_dead;
   p.n = g->n;
   p.nwords = w->nwords;
   p.nnz = g->nnz;

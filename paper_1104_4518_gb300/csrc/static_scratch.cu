@@ -36,7 +36,7 @@ constexpr size_t kOffChunks = kOffVis + kBitsBytes;
 constexpr size_t kOffCtr = kOffChunks + 2 * kChunkBytes;
 constexpr size_t kOffBarrier = kOffCtr + kCtrBytes;
 constexpr size_t kOffSmall = kOffBarrier + kBarrierBytes;
-constexpr size_t kScratchBytes = kOffSmall + kSmallBytes;  // about 13.2 MB
+constexpr size_t kScratchBytes = kOffSmall + kSmallBytes;  // 15,287,296 bytes
 
 // The scratch shared by every call in this process (zero-initialised at module load).
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
