@@ -96,7 +96,8 @@ typedef struct bfs_tuning {
                                  (1..8, default 4) */
   int32_t chunk_degree;  /* top-down: vertices above this degree are split into grid-wide chunks of 1024
                             edges (>= 1024, default 1024) */
-  float alpha;           /* heuristic: go PULL when frontier edges > unvisited edges / alpha (default 14) */
+  float alpha;           /* heuristic: go PULL when frontier edges > unvisited edges / alpha and the
+                            frontier grows (default 100) */
   float beta;            /* heuristic: leave PULL when frontier count < n / beta (default 24) */
   int32_t batch_topdown_limit; /* batched: levels with at most this many active vertices expand top-down (default n/64) */
   int32_t reserved;

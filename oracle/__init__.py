@@ -7,6 +7,9 @@ in `paper_1104_4518_gb300.inputs` are the only module both sides use, and they
 hold none of the method's arithmetic).
 
 Contents
+  - `validate_edges`: an O(m) check of a BFS result against the edge list
+    (distances and max-id parents), for sizes where building the oracle CSR
+    would take minutes.
   - `csr`, `bfs`, `component_edges`, `level_stats`: ctypes wrappers over the
     plain serial C in `bfs_oracle.c` (definitions of Sec. 2.1 / Algorithm 1 and
     the max-id parent of Sec. 3.2 / Algorithm 3).
@@ -57,6 +60,9 @@ def _load():
             lib.oracle_component_edges.argtypes = [i64p, i32p, ctypes.c_int32]
             lib.oracle_level_stats.restype = ctypes.c_int
             lib.oracle_level_stats.argtypes = [i64p, i32p, ctypes.c_int32, ctypes.c_int32, i64p, i64p]
+            lib.oracle_validate_edges.restype = ctypes.c_int64
+            lib.oracle_validate_edges.argtypes = [i32p, i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i32p,
+                                                  i32p, i32p, i64p]
             _lib = lib
     return _lib
 
@@ -140,6 +146,28 @@ def level_stats(g: CSR, level: np.ndarray, nlevels: int):
     _load().oracle_level_stats(_p(g.offsets, ctypes.c_int64), _p(level, ctypes.c_int32), g.n, nlevels,
                                _p(count, ctypes.c_int64), _p(edges, ctypes.c_int64))
     return count[:nlevels], edges[:nlevels]
+
+
+def validate_edges(src, dst, n: int, s: int, level: np.ndarray, parent: np.ndarray):
+    """Violations (a, b, c-parent, c-unreached) of a BFS result against an edge list.
+
+    O(m + n) check that needs no CSR (see oracle_validate_edges in bfs_oracle.c):
+    all four counts are zero exactly when `level` are the hop distances from s and
+    `parent` follows the max-id rule.  The C loop drops the GIL, so several
+    results can be validated on a thread pool.
+    """
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    best = np.empty(n, dtype=np.int32)
+    bad = np.zeros(4, dtype=np.int64)
+    r = _load().oracle_validate_edges(_p(src, ctypes.c_int32), _p(dst, ctypes.c_int32), int(src.shape[0]), n, int(s),
+                                      _p(level, ctypes.c_int32), _p(parent, ctypes.c_int32), _p(best, ctypes.c_int32),
+                                      _p(bad, ctypes.c_int64))
+    if r < 0:
+        raise ValueError("oracle_validate_edges: bad argument")
+    return bad
 
 
 # ---------------- Algorithm 3 on one process, pure Python ----------------

@@ -148,3 +148,50 @@ int oracle_level_stats(const int64_t* offsets, const int32_t* level, int32_t n, 
   }
   return 0;
 }
+
+/*
+ * Checks a BFS result against an edge list, in O(m + n), without building a
+ * CSR.  The result is accepted when
+ *   (a) level[s] = 0 and parent[s] = s;
+ *   (b) for every non-loop edge (u, v): level[u] = -1 exactly when level[v] = -1,
+ *       and |level[u] - level[v]| <= 1;
+ *   (c) every reached v != s has a neighbour one level closer to s, and
+ *       parent[v] is the largest such neighbour; unreached vertices have
+ *       parent -1.
+ * (a)-(c) make level the hop distance: following parents gives a path of
+ * length level[v], so d(s, v) <= level[v]; along any path from s the level
+ * grows by at most one per edge, so level[v] <= d(s, v).  (c) is the max-id
+ * parent rule of Sec. 3.2 itself.
+ * best: int32 scratch[n].  bad[0..3] receive the violations of (a), (b),
+ * (c)-parent and (c)-unreached; returns their sum, or -1 on a bad argument.
+ */
+int64_t oracle_validate_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, int32_t s,
+                              const int32_t* level, const int32_t* parent, int32_t* best, int64_t* bad) {
+  if (n <= 0 || s < 0 || s >= n || !level || !parent || !best || !bad || (m > 0 && (!src || !dst))) return -1;
+  for (int i = 0; i < 4; ++i) bad[i] = 0;
+  if (level[s] != 0 || parent[s] != s) bad[0] += 1;
+  for (int32_t v = 0; v < n; ++v) best[v] = -1;
+  for (int64_t e = 0; e < m; ++e) {
+    int32_t u = src[e], v = dst[e];
+    if (u < 0 || u >= n || v < 0 || v >= n) return -1;
+    if (u == v) continue;
+    int32_t lu = level[u], lv = level[v];
+    if ((lu < 0) != (lv < 0)) {
+      bad[1] += 1;
+      continue;
+    }
+    if (lu < 0) continue;
+    if (lu - lv > 1 || lv - lu > 1) bad[1] += 1;
+    if (lu == lv - 1 && u > best[v]) best[v] = u;
+    if (lv == lu - 1 && v > best[u]) best[u] = v;
+  }
+  for (int32_t v = 0; v < n; ++v) {
+    if (v == s) continue;
+    if (level[v] > 0) {
+      if (best[v] < 0 || parent[v] != best[v]) bad[2] += 1;
+    } else if (level[v] == 0 || parent[v] != -1 || level[v] < -1) {
+      bad[3] += 1;
+    }
+  }
+  return bad[0] + bad[1] + bad[2] + bad[3];
+}

@@ -379,6 +379,35 @@ def bfs_autotune(g: Graph, roots, stream=None) -> bfs_tuning:
     return t
 
 
+def graph_class(g: Graph) -> str:
+    """Cache key of a graph's tuning: the size class (log2 n, average degree)."""
+    n, nnz, _ = g.info()
+    import math
+    return f"n2^{max(0, int(round(math.log2(max(n, 1)))))}-deg{int(round(nnz / max(n, 1)))}"
+
+
+def bfs_autotune_cached(g: Graph, roots, cache_path: str, stream=None) -> bfs_tuning:
+    """bfs_autotune with a JSON cache keyed by (graph class, GPU name): a hit sets the
+    cached tuning on the graph without timing anything."""
+    import json
+    torch = _torch()
+    key = f"{graph_class(g)}|{torch.cuda.get_device_name()}"
+    cache = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    if key in cache:
+        bfs_set_tuning(g, **cache[key])
+        return bfs_get_tuning(g)
+    t = bfs_autotune(g, roots, stream)
+    cache[key] = t.as_dict()
+    tmp = cache_path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, cache_path)
+    return t
+
+
 # ---------------- selector network ----------------
 
 def bfs_mlp_forward(params, X, Y, stream=None):

@@ -76,7 +76,7 @@ bfs_tuning effective_tuning(const bfs_graph* g) {
   if (t.pull_thread_degree > 8) t.pull_thread_degree = 8;
   if (t.chunk_degree <= 0) t.chunk_degree = 1024;
   if (t.chunk_degree < kChunkEdges) t.chunk_degree = kChunkEdges;
-  if (!(t.alpha > 0.0f)) t.alpha = 14.0f;
+  if (!(t.alpha > 0.0f)) t.alpha = 100.0f;
   if (!(t.beta > 0.0f)) t.beta = 24.0f;
   if (t.batch_topdown_limit <= 0) t.batch_topdown_limit = std::max(1024, g->n / 64);
   return t;
@@ -206,12 +206,14 @@ static int make_graph_from_device_csr(int64_t* d_off, int32_t* d_adj, int32_t n,
   }
   int rc = dev_alloc((void**)&g->d_dead, sizeof(uint32_t) * (((size_t)n + 31) / 32), "edgeless-vertex bitmap");
   if (!rc) rc = compute_dead_bits(d_off, n, g->d_dead, nullptr);
+  if (!rc) rc = build_big_chunks(d_off, n, nnz, nullptr, &g->d_big, &g->nbig);
   if (!rc) {
     err = cudaDeviceSynchronize();
     if (err != cudaSuccess) rc = cuda_fail(err, "edgeless-vertex bitmap");
   }
   if (rc) {
     if (g->d_dead) cudaFree(g->d_dead);
+    if (g->d_big) cudaFree(g->d_big);
     cudaFree(g->d_part_base);
     delete g;
     return rc;
@@ -402,6 +404,7 @@ void bfs_graph_destroy(bfs_graph* g) {
   if (g->d_adj) cudaFree(g->d_adj);
   if (g->d_part_base) cudaFree(g->d_part_base);
   if (g->d_dead) cudaFree(g->d_dead);
+  if (g->d_big) cudaFree(g->d_big);
   delete g;
 }
 
@@ -715,7 +718,7 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
     const int cd[] = {128, 256, 1024};
     const int pd[] = {1, 2, 4, 6, 8};
     const int ch[] = {1024, 4096, 16384};
-    const float al[] = {4.0f, 8.0f, 14.0f, 24.0f, 48.0f};
+    const float al[] = {14.0f, 32.0f, 100.0f, 300.0f, 1000.0f};
     const float be[] = {8.0f, 16.0f, 24.0f, 48.0f, 96.0f};
     for (int knob = 0; knob < 6 && !rc; ++knob) {
       const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 5 : knob == 3 ? 3 : 5;

@@ -9,14 +9,20 @@
 // with bit r in F_k[u], found by scanning v's sorted row from the largest id
 // down and masking off the bits already resolved.
 //
-// Two ways to expand a level (identical results):
-//   pull     : every vertex not yet reached by all roots scans its row (one
-//              phase); short rows lane by lane, long rows by the whole warp;
-//   top-down : the frontier's rows OR their bits into F_{k+1} of unreached
-//              neighbours (the first writer enqueues the neighbour; rows above
-//              kChunkEdges entries are split into chunks, one CTA each), then
-//              every queued vertex resolves its parents with the same
-//              descending scan (two phases).
+// "Reached before level k+1" is tested as V | F_k, so V only has to absorb a
+// frontier's bits during the level that expands it, and every level is one
+// phase.  Two ways to expand a level (identical results):
+//   pull     : every vertex not yet reached by all roots scans its row; short
+//              rows lane by lane, rows up to kChunkEdges entries by the whole
+//              warp, longer rows in kChunkEdges-entry chunks (a static table
+//              built with the graph), one CTA per chunk, the chunks combining
+//              through atomicMax on the parents and atomicOr on F_{k+1};
+//   top-down : every frontier row ORs its bits into F_{k+1} of unreached
+//              neighbours and offers itself as their parent with atomicMax
+//              for each new root bit (every frontier neighbour offers, so the
+//              largest id wins); the first writer of a root bit writes the
+//              level, the first writer of any bit enqueues the neighbour.
+//              Rows above kChunkEdges entries are split into chunk items.
 // Output rows are root-major: level[r * n + v], parent[r * n + v].
 #include <cooperative_groups.h>
 
@@ -48,6 +54,8 @@ struct BatchParams {
   uint64_t* V;
   int32_t* queue[3];
   int64_t* chunks[2];
+  const int64_t* big;  // chunks of rows longer than kChunkEdges (static, per graph)
+  long long nbig;
   LevelCtr* ctr;
   bfsdev::GridBarrier* bar;
   int* status;
@@ -170,17 +178,74 @@ __device__ __forceinline__ uint64_t resolve_group(const BatchParams& p, const ui
   return found;
 }
 
-// Top-down discover of edge (u -> w) with frontier bits f.
-__device__ __forceinline__ void discover(const BatchParams& p, uint64_t* Fn, int knext, uint64_t f, int w) {
-  const uint64_t nb = f & ~p.V[w];
-  if (!nb || (Fn[w] & nb) == nb) return;
+// Top-down visit of edge (u -> w) with frontier bits f of u at level knext - 1.
+__device__ __forceinline__ void td_visit(const BatchParams& p, const uint64_t* Fc, uint64_t* Fn, int knext,
+                                         uint64_t f, int u, int w) {
+  const uint64_t nb = f & ~(p.V[w] | Fc[w]);
+  if (!nb) return;
+  for (uint64_t b = nb; b;) {  // u is a parent candidate of w for every new root bit
+    const int r = __ffsll((long long)b) - 1;
+    b &= b - 1;
+    atomicMax(&p.parent[(long long)r * p.n + w], u);
+  }
+  if ((Fn[w] & nb) == nb) return;
   const unsigned long long old = atomicOr((unsigned long long*)&Fn[w], (unsigned long long)nb);
+  for (uint64_t b = nb & ~old; b;) {
+    const int r = __ffsll((long long)b) - 1;
+    b &= b - 1;
+    p.level[(long long)r * p.n + w] = knext;
+  }
   if (old == 0) {
     cg::coalesced_group g = cg::coalesced_threads();
     unsigned base = 0;
     if (g.thread_rank() == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)g.size());
     base = g.shfl(base, 0);
     p.queue[knext % 3][base + g.thread_rank()] = w;
+    const long long deg = __ldg(&p.off[w + 1]) - __ldg(&p.off[w]);
+    if (deg > kChunkEdges) push_chunks(p, knext, w, deg);
+  }
+}
+
+// Pull over one kChunkEdges-entry chunk of a long row of v by a whole CTA:
+// each warp takes 64 consecutive entries (two steps of 32, from the top),
+// finds for every root bit of `need` its highest hit, and combines with the
+// other warps and chunks through atomicMax (parents) and atomicOr (F_{k+1}).
+__device__ __forceinline__ void pull_big_chunk(const BatchParams& p, const uint64_t* Fc, uint64_t* Fn, int knext,
+                                               int v, long long rb, long long re, uint64_t need, int lane, int wid) {
+  uint64_t found = 0;
+#pragma unroll
+  for (int step = 0; step < 2; ++step) {
+    const long long j = re - 1 - (long long)wid * 64 - step * 32 - lane;
+    int u = 0;
+    uint64_t f = 0;
+    if (j >= rb) {
+      u = __ldg(&p.adj[j]);
+      f = Fc[u] & need;
+    }
+    const unsigned lo = __reduce_or_sync(kFull, (unsigned)f);
+    const unsigned hi = __reduce_or_sync(kFull, (unsigned)(f >> 32));
+    uint64_t nb = (((uint64_t)hi << 32) | lo) & ~found;
+    found |= nb;
+    while (nb) {
+      const int r = __ffsll((long long)nb) - 1;
+      nb &= nb - 1;
+      const int src = __ffs(__ballot_sync(kFull, (f >> r) & 1ull)) - 1;
+      const int pu = __shfl_sync(kFull, u, src);
+      if (lane == 0) atomicMax(&p.parent[(long long)r * p.n + v], pu);
+    }
+  }
+  if (lane == 0 && found) {
+    const unsigned long long old = atomicOr((unsigned long long*)&Fn[v], (unsigned long long)found);
+    for (uint64_t b = found & ~old; b;) {
+      const int r = __ffsll((long long)b) - 1;
+      b &= b - 1;
+      p.level[(long long)r * p.n + v] = knext;
+    }
+    if (old == 0) {
+      const unsigned pos = atomicAdd(&p.ctr[knext % kCtrRing].count, 1u);
+      p.queue[knext % 3][pos] = v;
+      push_chunks(p, knext, v, __ldg(&p.off[v + 1]) - __ldg(&p.off[v]));
+    }
   }
 }
 
@@ -254,8 +319,9 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
     }
 
     const bool topdown = (long long)count <= p.td_limit;
+    const int wid = tid >> 5;
     if (topdown) {
-      // top-down discover: chunks of long rows (one CTA each), then one warp per short row
+      // frontier rows above kChunkEdges: one CTA per chunk item
       const int64_t* items = p.chunks[k & 1];
       for (long long ci = blockIdx.x; ci < nchunks; ci += G) {
         const int64_t it = items[ci];
@@ -263,58 +329,52 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         const long long rb = __ldg(&p.off[u]) + (it & 0xffffffffll) * kChunkEdges;
         const long long re = min(rb + (long long)kChunkEdges, (long long)__ldg(&p.off[u + 1]));
         const uint64_t f = Fc[u];
-        for (long long j = rb + tid; j < re; j += kBBlock) discover(p, Fn, knext, f, __ldg(&p.adj[j]));
+        for (long long j = rb + tid; j < re; j += kBBlock) td_visit(p, Fc, Fn, knext, f, u, __ldg(&p.adj[j]));
       }
+      // other frontier rows: one warp each; every frontier vertex folds its bits into V
       for (long long i = gwarp; i < count; i += gwarps) {
         const int u = Q[i];
+        const uint64_t f = Fc[u];
+        if (lane == 0) p.V[u] |= f;
         const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
         if (e - b > kChunkEdges) continue;
-        const uint64_t f = Fc[u];
-        for (long long j = b + lane; j < e; j += 32) discover(p, Fn, knext, f, __ldg(&p.adj[j]));
-      }
-      if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
-      // resolve parents of the newly reached (vertex, root) pairs, 32 queue entries per warp
-      const unsigned ncount = __ldcg(&p.ctr[knext % kCtrRing].count);
-      const int32_t* NQ = p.queue[knext % 3];
-      for (long long base = gwarp * 32; base < ncount; base += gwarps * 32) {
-        const long long i = base + lane;
-        int w = 0;
-        uint64_t need = 0;
-        long long b = 0, e = 0;
-        if (i < ncount) {
-          w = NQ[i];
-          need = Fn[w];
-          b = __ldg(&p.off[w]);
-          e = __ldg(&p.off[w + 1]);
-        }
-        resolve_group(p, Fc, w, b, e, need, knext, lane);
-        if (i < ncount) {
-          p.V[w] |= need;
-          if (e - b > kChunkEdges) push_chunks(p, knext, w, e - b);
-        }
+        for (long long j = b + lane; j < e; j += 32) td_visit(p, Fc, Fn, knext, f, u, __ldg(&p.adj[j]));
       }
     } else {
-      // pull: every vertex with unreached roots scans its row, 32 vertices per warp
+      // long rows: one CTA per chunk of the static table
+      for (long long ci = blockIdx.x; ci < p.nbig; ci += G) {
+        const int64_t it = p.big[ci];
+        const int v = (int)(it >> 32);
+        const uint64_t need = ~(p.V[v] | Fc[v]) & p.mask;
+        if (!need) continue;
+        const long long rb = __ldg(&p.off[v]) + (it & 0xffffffffll) * kChunkEdges;
+        const long long re = min(rb + (long long)kChunkEdges, (long long)__ldg(&p.off[v + 1]));
+        pull_big_chunk(p, Fc, Fn, knext, v, rb, re, need, lane, wid);
+      }
+      // other rows: 32 vertices per warp; the owner lane updates V and F_{k+1}
       const long long nw = ((long long)p.n + 31) / 32;
       for (long long ww = gwarp; ww < nw; ww += gwarps) {
         const long long v0 = ww * 32 + lane;
         const int v = (int)v0;
-        uint64_t need = 0;
+        uint64_t need = 0, vv = 0, fv = 0;
         long long b = 0, e = 0;
         if (v0 < p.n) {
-          need = ~p.V[v] & p.mask;
+          vv = p.V[v];
+          fv = Fc[v];
+          need = ~(vv | fv) & p.mask;
           if (need) {
             b = __ldg(&p.off[v]);
             e = __ldg(&p.off[v + 1]);
-            if (e == b) need = 0;
+            if (e == b || e - b > kChunkEdges) need = 0;
           }
         }
         const uint64_t found = resolve_group(p, Fc, v, b, e, need, knext, lane);
-        if (found) {
-          Fn[v] = found;
-          p.V[v] |= found;
+        if (v0 < p.n) {
+          const uint64_t nv = vv | fv | found;
+          if (nv != vv) p.V[v] = nv;
+          if (found) Fn[v] = found;
         }
-        enqueue_warp(p, knext, v, found != 0, e - b);
+        enqueue_warp(p, knext, v, found != 0, 0);
       }
     }
     if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
@@ -358,6 +418,8 @@ int launch_batch(const BatchRequest& r, cudaStream_t s) {
   p.V = w->bvis;
   p.chunks[0] = w->chunks[0];
   p.chunks[1] = w->chunks[1];
+  p.big = g->d_big;
+  p.nbig = g->nbig;
   p.ctr = w->ctr;
   p.bar = reinterpret_cast<bfsdev::GridBarrier*>(w->barrier);
   p.status = w->status;

@@ -344,6 +344,18 @@ __global__ void dead_bits_kernel(const int64_t* __restrict__ off, int32_t n, lon
   }
 }
 
+__global__ void big_chunks_kernel(const int64_t* __restrict__ off, int32_t n, int64_t* items,
+                                  unsigned long long* count) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const long long deg = off[v + 1] - off[v];
+    if (deg <= kChunkEdges) continue;
+    const unsigned long long nch = (unsigned long long)((deg + kChunkEdges - 1) / kChunkEdges);
+    const unsigned long long pos = atomicAdd(count, nch);
+    for (unsigned long long c = 0; c < nch; ++c) items[pos + c] = (v << 32) | (long long)c;
+  }
+}
+
 int bits_for(int32_t n) {
   int b = 1;
   while (b < 31 && ((int64_t)1 << b) < (int64_t)n) ++b;
@@ -468,6 +480,36 @@ int compute_dead_bits(const int64_t* d_off, int32_t n, uint32_t* d_dead, cudaStr
   if (int e = current_device_info(&di)) return e;
   dead_bits_kernel<<<di.sm_count * 4, 256, 0, s>>>(d_off, n, ((long long)n + 31) / 32, d_dead);
   BFS_CUDA_TRY(cudaGetLastError());
+  return BFS_OK;
+}
+
+int build_big_chunks(const int64_t* d_off, int32_t n, int64_t nnz, cudaStream_t s, int64_t** items_out,
+                     int64_t* count_out) {
+  DeviceInfo di;
+  if (int e = current_device_info(&di)) return e;
+  const long long cap = 2 * (nnz / kChunkEdges) + 2;  // sum of ceil(deg / C) over rows with deg > C
+  int64_t* items = nullptr;
+  unsigned long long* d_count = nullptr;
+  if (int e = dev_alloc((void**)&items, sizeof(int64_t) * cap, "high-degree row chunks")) return e;
+  if (int e = dev_alloc((void**)&d_count, sizeof(unsigned long long), "chunk count")) {
+    cudaFree(items);
+    return e;
+  }
+  unsigned long long cnt = 0;
+  cudaError_t err = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s);
+  if (err == cudaSuccess) {
+    big_chunks_kernel<<<di.sm_count * 4, 256, 0, s>>>(d_off, n, items, d_count);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&cnt, d_count, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  cudaFree(d_count);
+  if (err != cudaSuccess) {
+    cudaFree(items);
+    return cuda_fail(err, "high-degree row chunks");
+  }
+  *items_out = items;
+  *count_out = (int64_t)cnt;
   return BFS_OK;
 }
 

@@ -96,6 +96,8 @@ struct bfs_graph {
   int64_t* d_off = nullptr;
   int32_t* d_adj = nullptr;
   uint32_t* d_dead = nullptr;  // bitmap of vertices without edges (tail bits set)
+  int64_t* d_big = nullptr;    // (v << 32 | c) for every kChunkEdges-entry chunk c of rows longer than kChunkEdges
+  int64_t nbig = 0;
   int32_t parts = 1;
   std::vector<int64_t> part_base;  // parts + 1 entries (union graphs)
   int64_t* d_part_base = nullptr;
@@ -124,6 +126,8 @@ int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, 
                          cudaStream_t s, int64_t** d_off, int32_t** d_adj, int64_t* nnz);
 // Bitmap of the vertices without edges (bits beyond n set), one word per 32 vertices.
 int compute_dead_bits(const int64_t* d_off, int32_t n, uint32_t* d_dead, cudaStream_t s);
+// Chunk items of every row longer than kChunkEdges (order unspecified); *count receives their number.
+int build_big_chunks(const int64_t* d_off, int32_t n, int64_t nnz, cudaStream_t s, int64_t** items, int64_t* count);
 // Adds off_shift to n_part offsets and id_shift to nnz_part ids (union building).
 int union_shift(int64_t* off, int32_t* adj, int64_t n_part, int64_t nnz_part, int64_t off_shift, int32_t id_shift,
                 cudaStream_t s);

@@ -49,6 +49,8 @@ using bfsdev::kFull;
 
 constexpr int kBlock = 512;
 constexpr int kWarps = kBlock / 32;
+constexpr int kQBuf = 2048;   // per-CTA buffer of next-frontier vertices (top-down claims)
+constexpr int kWQBuf = 256;   // per-warp buffer of next-frontier vertices (pull claims)
 
 #ifdef BFS_PHASE_TIMING
 // Diagnostic build only: global-timer stamps of the first 4096 levels.
@@ -130,21 +132,33 @@ __device__ __forceinline__ void push_chunks(const LoopParams& p, int knext, int 
   for (unsigned c = 0; c < nch; ++c) dst[pos + c] = ((int64_t)v << 32) | (int64_t)c;
 }
 
+// Appends w to the CTA's next-frontier buffer (shared memory); when the buffer
+// is full the vertex goes straight to the global queue.
+__device__ __forceinline__ void cta_enqueue(const LoopParams& p, int knext, int* qn, int* cq, int w) {
+  const int pos = atomicAdd(qn, 1);
+  if (pos < kQBuf) {
+    cq[pos] = w;
+  } else {  // buffer full: one global atomic per group of converged threads
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)g.size());
+    base = g.shfl(base, 0);
+    p.queue[knext % 3][base + g.thread_rank()] = w;
+  }
+}
+
 // Bookkeeping of a vertex claimed for level knext (the caller already set nxt).
-__device__ __forceinline__ void claim_topdown(const LoopParams& p, int knext, int w, long long deg, Acc& acc) {
+__device__ __forceinline__ void claim_topdown(const LoopParams& p, int knext, int w, long long deg, Acc& acc,
+                                              int* qn, int* cq) {
   p.level[w] = knext;
-  cg::coalesced_group g = cg::coalesced_threads();
-  unsigned base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)g.size());
-  base = g.shfl(base, 0);
-  p.queue[knext % 3][base + g.thread_rank()] = w;
+  cta_enqueue(p, knext, qn, cq, w);
   acc_vertex(acc, deg);
   if (deg > p.chunk_deg) push_chunks(p, knext, w, deg);
 }
 
 // Top-down visit of edge (u -> w) in phase k.
 __device__ __forceinline__ void td_visit(const LoopParams& p, const uint32_t* cur, uint32_t* nxt, int k,
-                                         int u, int w, Acc& acc) {
+                                         int u, int w, Acc& acc, int* qn, int* cq) {
   const int ww = w >> 5;
   const uint32_t m = 1u << (w & 31);
   const uint32_t vw = p.vis[ww], cw = cur[ww], nw = nxt[ww];  // independent loads, one round trip
@@ -154,7 +168,7 @@ __device__ __forceinline__ void td_visit(const LoopParams& p, const uint32_t* cu
   const long long wb = __ldg(&p.off[w]), we = __ldg(&p.off[w + 1]);  // speculative: the claim needs the degree
   const uint32_t old = atomicOr(&nxt[ww], m);
   if (old & m) return;
-  claim_topdown(p, k + 1, w, we - wb, acc);
+  claim_topdown(p, k + 1, w, we - wb, acc, qn, cq);
 }
 
 // Warp-cooperative descending scan of the rows still open in a warp: lane r
@@ -219,25 +233,37 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
   return v;
 }
 
-// Adds the CTA's accumulated counters into level knext's slot.
-__device__ __forceinline__ void flush_acc(const LoopParams& p, int knext, Acc& acc, unsigned long long* s_acc) {
+// End of a phase for one CTA: adds its counters into level knext's slot and
+// moves its buffered next-frontier vertices to the global queue with a single
+// atomic.  CTAs that claimed nothing skip all of it.
+template <typename S>
+__device__ __forceinline__ void end_phase(const LoopParams& p, int knext, Acc& acc, S& sm) {
+  const bool mine = (acc.edges | acc.b0 | acc.b1 | acc.b2) != 0;
+  if (!__syncthreads_or(mine) && sm.qn == 0) return;
   const unsigned long long e = warp_sum_u64(acc.edges), b0 = warp_sum_u64(acc.b0), b1 = warp_sum_u64(acc.b1),
                            b2 = warp_sum_u64(acc.b2);
   if ((threadIdx.x & 31) == 0 && (e | b0 | b1 | b2)) {
-    atomicAdd(&s_acc[0], e);
-    atomicAdd(&s_acc[1], b0);
-    atomicAdd(&s_acc[2], b1);
-    atomicAdd(&s_acc[3], b2);
+    atomicAdd(&sm.acc[0], e);
+    atomicAdd(&sm.acc[1], b0);
+    atomicAdd(&sm.acc[2], b1);
+    atomicAdd(&sm.acc[3], b2);
   }
   __syncthreads();
+  const int nb = min(sm.qn, kQBuf);
   if (threadIdx.x == 0) {
     LevelCtr* c = &p.ctr[knext % kCtrRing];
-    if (s_acc[0]) atomicAdd(&c->edges, s_acc[0]);
-    if (s_acc[1]) atomicAdd(&c->bins[0], s_acc[1]);
-    if (s_acc[2]) atomicAdd(&c->bins[1], s_acc[2]);
-    if (s_acc[3]) atomicAdd(&c->bins[2], s_acc[3]);
-    s_acc[0] = s_acc[1] = s_acc[2] = s_acc[3] = 0;
+    if (sm.acc[0]) atomicAdd(&c->edges, sm.acc[0]);
+    if (sm.acc[1]) atomicAdd(&c->bins[0], sm.acc[1]);
+    if (sm.acc[2]) atomicAdd(&c->bins[1], sm.acc[2]);
+    if (sm.acc[3]) atomicAdd(&c->bins[2], sm.acc[3]);
+    sm.acc[0] = sm.acc[1] = sm.acc[2] = sm.acc[3] = 0;
+    if (nb) sm.qbase = atomicAdd(&c->count, (unsigned)nb);
   }
+  __syncthreads();
+  int32_t* Q = p.queue[knext % 3];
+  for (int i = threadIdx.x; i < nb; i += kBlock) Q[sm.qbase + i] = sm.cq[i];
+  __syncthreads();
+  if (threadIdx.x == 0) sm.qn = 0;
   acc = Acc{};
 }
 
@@ -279,7 +305,10 @@ struct Smem {
   int tu[kBlock];
   long long tb[kBlock];
   int tpref[kBlock + 1];
-  int qbuf[kWarps][64];
+  int wq[kWarps][kWQBuf];  // per warp: next-frontier vertices claimed by the pull phase
+  int qn;                // entries in cq (may exceed kQBuf: the excess went straight to the queue)
+  unsigned qbase;
+  int cq[kQBuf];         // the CTA's share of the next frontier queue, flushed once per phase
   float x[12];
   float h1[64];
   float h2[64];
@@ -304,7 +333,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
     const long long rb = __ldg(&p.off[v]), re = __ldg(&p.off[v + 1]);
     const long long b = rb + c * kChunkEdges;
     const long long e = min(b + (long long)kChunkEdges, re);
-    for (long long j = b + tid; j < e; j += kBlock) td_visit(p, cur, nxt, k, v, __ldg(&p.adj[j]), acc);
+    for (long long j = b + tid; j < e; j += kBlock) td_visit(p, cur, nxt, k, v, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
   }
 
   // frontier entry i goes to CTA i % G, so that small frontiers spread over every SM
@@ -316,7 +345,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
       atomicOr(&p.vis[u >> 5], 1u << (u & 31));
       const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
       if (e - b > p.chunk_deg) continue;
-      for (long long j = b; j < e; ++j) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc);
+      for (long long j = b; j < e; ++j) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
     }
   } else if (variant == BFS_VARIANT_TD_WARP) {
     const long long gwarps = gthreads / 32;
@@ -325,7 +354,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
       if (lane == 0) atomicOr(&p.vis[u >> 5], 1u << (u & 31));
       const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
       if (e - b > p.chunk_deg) continue;
-      for (long long j = b + lane; j < e; j += 32) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc);
+      for (long long j = b + lane; j < e; j += 32) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
     }
   } else {  // BFS_VARIANT_TD_BINNED
     for (long long tile = 0; tile < count; tile += gthreads) {
@@ -355,7 +384,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
         __syncthreads();
         const int cu = sm.cu;
         const long long cb = sm.cb, ce = sm.ce;
-        for (long long j = cb + tid; j < ce; j += kBlock) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc);
+        for (long long j = cb + tid; j < ce; j += kBlock) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
         __syncthreads();
         if (tid == 0) sm.owner = -1;
         __syncthreads();
@@ -368,7 +397,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
         const int cu = __shfl_sync(kFull, u, l);
         const long long cb = __shfl_sync(kFull, b, l), ce = __shfl_sync(kFull, e, l);
         if (lane == l) u = -1;
-        for (long long j = cb + lane; j < ce; j += 32) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc);
+        for (long long j = cb + lane; j < ce; j += 32) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
       }
       // thread bin: the CTA gathers the remaining short rows edge by edge
       const int sdeg = u >= 0 ? (int)deg : 0;
@@ -389,7 +418,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
             else hi = mid;
           }
           const int ou = sm.tu[lo];
-          td_visit(p, cur, nxt, k, ou, __ldg(&p.adj[sm.tb[lo] + (idx - sm.tpref[lo])]), acc);
+          td_visit(p, cur, nxt, k, ou, __ldg(&p.adj[sm.tb[lo] + (idx - sm.tpref[lo])]), acc, &sm.qn, sm.cq);
         }
       }
       __syncthreads();
@@ -398,27 +427,22 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
 }
 
 // ---------------- pull phase ----------------
-// Appends a warp's claimed vertices through a 64-entry shared buffer: one
-// queue atomic per 32 vertices instead of one per bitmap word.
-__device__ __forceinline__ void pull_enqueue(const LoopParams& p, int knext, int* qbuf, int& nbuf, bool claimed,
-                                             int v, int lane, bool flush_all) {
+// Appends the claimed vertices of a warp (one per lane where `claimed`) to the
+// warp's buffer in shared memory; once it holds at least kWQBuf - 32 vertices
+// (or at the end of the phase) they move to the queue with one atomic.
+__device__ __forceinline__ void warp_enqueue(const LoopParams& p, int knext, int* wq, int& nbuf, bool claimed, int v,
+                                             int lane, bool flush) {
   const unsigned hm = __ballot_sync(kFull, claimed);
-  if (claimed) qbuf[nbuf + __popc(hm & bfsdev::lanemask_lt())] = v;
+  if (claimed) wq[nbuf + __popc(hm & bfsdev::lanemask_lt())] = v;
   nbuf += __popc(hm);
+  if (nbuf == 0 || (!flush && nbuf < kWQBuf - 32)) return;
   __syncwarp();
-  while (nbuf >= 32 || (flush_all && nbuf > 0)) {
-    const int take = min(nbuf, 32);
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)take);
-    base = __shfl_sync(kFull, base, 0);
-    int moved = 0;
-    if (lane < take) p.queue[knext % 3][base + lane] = qbuf[lane];
-    if (lane + 32 < nbuf) moved = qbuf[lane + 32];
-    __syncwarp();
-    if (lane + 32 < nbuf) qbuf[lane] = moved;
-    __syncwarp();
-    nbuf -= take;
-  }
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)nbuf);
+  base = __shfl_sync(kFull, base, 0);
+  for (int i = lane; i < nbuf; i += 32) p.queue[knext % 3][base + i] = wq[i];
+  __syncwarp();
+  nbuf = 0;
 }
 
 __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
@@ -428,7 +452,7 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
   const long long gwarps = (long long)gridDim.x * kWarps;
   const int knext = k + 1;
   const int probe = p.pull_thread_deg;
-  int* qbuf = sm.qbuf[wid];
+  int* wq = sm.wq[wid];
   int nbuf = 0;
   for (long long ww = ((long long)blockIdx.x * kBlock + threadIdx.x) / 32; ww < p.nwords; ww += gwarps) {
     const uint32_t vw = p.vis[ww];
@@ -475,17 +499,20 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
       acc_vertex(acc, deg);
       if (deg > p.chunk_deg) push_chunks(p, knext, v, deg);
     }
-    if (hits) pull_enqueue(p, knext, qbuf, nbuf, hit >= 0, v, lane, false);
+    if (hits) warp_enqueue(p, knext, wq, nbuf, hit >= 0, v, lane, false);
   }
-  pull_enqueue(p, knext, qbuf, nbuf, false, 0, lane, true);
+  warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
 }
 
+// Direction choice in the manner of direction-optimising BFS: go pull when the
+// frontier's edges exceed the unvisited edges / alpha while the frontier is
+// growing, leave pull when the frontier falls below n / beta.
 __device__ __forceinline__ int heuristic_variant(const LoopParams& p, int prev_variant, long long count,
-                                                 long long edges, long long unvisited_edges,
-                                                 const long long* bins) {
+                                                 long long prev_count, long long edges,
+                                                 long long unvisited_edges) {
   bool pull;
   if (prev_variant == BFS_VARIANT_PULL) pull = (float)count * p.beta >= (float)p.n;
-  else pull = (float)edges * p.alpha > (float)unvisited_edges;
+  else pull = (float)edges * p.alpha > (float)unvisited_edges && count >= prev_count;
   return pull ? BFS_VARIANT_PULL : BFS_VARIANT_TD_BINNED;
 }
 
@@ -497,6 +524,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   if (tid == 0) {
     epoch = bfsdev::ld_acquire_u32(&p.bar->epoch);
     sm.owner = -1;
+    sm.qn = 0;
     sm.acc[0] = sm.acc[1] = sm.acc[2] = sm.acc[3] = 0;
   }
   const bool learned = p.selector == BFS_SELECT_LEARNED && p.mlp != nullptr;
@@ -560,7 +588,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
         if (deg > p.chunk_deg) push_chunks(p, 0, s, deg);
       }
       if (tid == 0) p.ctr[0].count = (unsigned)p.nsources;
-      flush_acc(p, 0, acc, sm.acc);
+      end_phase(p, 0, acc, sm);
     }
     if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
   }
@@ -568,19 +596,22 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   // ---- level loop
   long long cum_count = 0, cum_edges = 0;
   int prev_variant = -1;
+  unsigned prev_count = 0;
   uint64_t t_prev = 0;
   if (blockIdx.x == 0 && tid == 0) t_prev = bfsdev::global_timer_ns();
   int k = 0;
   Acc acc;
   for (;; ++k) {
     PHASE_TS(k, 0);
+    // one round of loads: the counters of f_k and the first entry of f_{k-1} to recycle
     const LevelCtr* c = &p.ctr[k % kCtrRing];
     const unsigned count = __ldcg(&c->count);
-    if (count == 0) break;
     const unsigned nchunks = __ldcg(&c->chunks);
     const long long edges = (long long)__ldcg(&c->edges);
-    long long bins[3] = {(long long)__ldcg(&c->bins[0]), (long long)__ldcg(&c->bins[1]),
-                         (long long)__ldcg(&c->bins[2])};
+    const bool sparse_clr = k >= 1 && (long long)prev_count * 4 < p.nwords;
+    const int32_t* PQ = p.queue[(k + 2) % 3];
+    const int clr0 = (sparse_clr && gtid < prev_count) ? PQ[gtid] : -1;
+    if (count == 0) break;
     cum_count += count;
     cum_edges += edges;
     const long long unvisited = (long long)p.n - cum_count;
@@ -592,8 +623,11 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
     } else if (p.selector == BFS_SELECT_SCHEDULE && k < p.schedule_len) {
       variant = p.schedule[k];
     } else if (learned) {
-      if (tid == 0)
+      if (tid == 0) {
+        const long long bins[3] = {(long long)__ldcg(&c->bins[0]), (long long)__ldcg(&c->bins[1]),
+                                   (long long)__ldcg(&c->bins[2])};
         bfsdev::level_features(p.n, p.nnz, k, count, edges, unvisited, unvisited_edges, bins, sm.x);
+      }
       __syncthreads();
       if (tid < 64) sm.h1[tid] = bfsdev::mlp_h1(s_mlp, sm.x, tid);
       __syncthreads();
@@ -610,7 +644,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
       __syncthreads();
       variant = sm.choice;
     } else {
-      variant = heuristic_variant(p, prev_variant, count, edges, unvisited_edges, bins);
+      variant = heuristic_variant(p, prev_variant, count, prev_count, edges, unvisited_edges);
     }
     if (variant < 0 || variant >= BFS_NUM_VARIANTS) variant = BFS_VARIANT_TD_BINNED;
 
@@ -620,20 +654,18 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
       reinterpret_cast<unsigned long long*>(&p.ctr[(k + 4) % kCtrRing])[tid] = 0ull;
     if (k >= 1) {
       uint32_t* clr = p.bits[(k + 2) % 3];
-      const unsigned prev_count = __ldcg(&p.ctr[(k + kCtrRing - 1) % kCtrRing].count);
-      if ((long long)prev_count * 4 < p.nwords) {
-        const int32_t* PQ = p.queue[(k + 2) % 3];
-        for (long long i = gtid; i < prev_count; i += gthreads) clr[PQ[i] >> 5] = 0u;
+      if (sparse_clr) {
+        if (clr0 >= 0) clr[clr0 >> 5] = 0u;
+        for (long long i = gtid + gthreads; i < prev_count; i += gthreads) clr[PQ[i] >> 5] = 0u;
       } else {
         for (long long w = gtid; w < p.nwords; w += gthreads) clr[w] = 0u;
       }
     }
-
     PHASE_TS(k, 2);
     if (variant == BFS_VARIANT_PULL) pull_phase(p, k, sm, acc);
     else topdown_phase(p, k, variant, count, nchunks, sm, acc);
     PHASE_TS(k, 3);
-    flush_acc(p, k + 1, acc, sm.acc);
+    end_phase(p, k + 1, acc, sm);
     PHASE_TS(k, 4);
     PHASE_ARRIVAL(k);
     if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
@@ -644,9 +676,9 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
       bfs_level_stat st;
       st.frontier_count = count;
       st.frontier_edges = edges;
-      st.bin_count[0] = bins[0];
-      st.bin_count[1] = bins[1];
-      st.bin_count[2] = bins[2];
+      st.bin_count[0] = (int64_t)__ldcg(&c->bins[0]);  // level k's slot is recycled only in phase k + 4
+      st.bin_count[1] = (int64_t)__ldcg(&c->bins[1]);
+      st.bin_count[2] = (int64_t)__ldcg(&c->bins[2]);
       st.unvisited_count = unvisited;
       st.unvisited_edges = unvisited_edges;
       st.time_ns = (int64_t)(t - t_prev);
@@ -656,6 +688,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
       t_prev = t;
     }
     prev_variant = variant;
+    prev_count = count;
   }
 
   if (gtid == 0) {

@@ -242,3 +242,25 @@ def test_device_wait_limit_returns_timeout_and_recovers():
         bfs.bfs_sync(g)
     assert e.value.code == bfs.BFS_ERR_TIMEOUT
     assert_same(oracle.bfs(og, s), run_gpu(g, s))
+
+
+# ---------------- autotuner ----------------
+
+def test_autotune_keeps_results_and_caches(tmp_path):
+    el, roots = inputs.workload_rmat(16, 4, graph_seed=1, root_seed=101)
+    og = oracle.csr_of(el)
+    g = device_graph_from_edges(el)
+    cache = str(tmp_path / "tuning.json")
+    t = bfs.bfs_autotune_cached(g, roots[:2], cache)
+    assert t.warp_degree in (8, 16, 32, 64) and 1 <= t.pull_thread_degree <= 8 and t.chunk_degree >= 1024
+    assert t.alpha > 0 and t.beta > 0 and t.batch_topdown_limit >= 1
+    for s in roots:
+        assert_same(oracle.bfs(og, int(s)), run_gpu(g, int(s)))
+    # a second graph of the same class takes the cached tuning without timing
+    g2 = device_graph_from_edges(el)
+    t2 = bfs.bfs_autotune_cached(g2, roots[:2], cache)
+    assert t2.as_dict() == t.as_dict()
+    parent, level = bfs.run_batch(g2, [int(s) for s in roots])
+    bfs.bfs_sync(g2)
+    for i, s in enumerate(roots):
+        assert_same(oracle.bfs(og, int(s)), (level[i].cpu().numpy(), parent[i].cpu().numpy()))

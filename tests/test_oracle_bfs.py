@@ -256,3 +256,41 @@ def test_planted_min_id_parent_is_caught():
         cands = [u for u in g.row(v) if level[u] == level[v] - 1]
         wrong[v] = min(cands)
     assert wrong[5] != 6 and parent[5] == 6
+
+
+# ---------------- the edge-list validator ----------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_validator_accepts_floyd_warshall_results(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(2, 60))
+    pairs = rng.integers(0, n, size=(int(rng.integers(0, 3 * n)), 2))
+    D = floyd_warshall(n, [tuple(p) for p in pairs])
+    for s in range(min(n, 5)):
+        el, ep = expected_from_distances(n, [tuple(p) for p in pairs], D, s)
+        bad = oracle.validate_edges(pairs[:, 0], pairs[:, 1], n, s, el, ep)
+        assert bad.sum() == 0
+
+
+def test_validator_catches_planted_mistakes():
+    el = inputs.rmat(10, 16, seed=21)
+    g = oracle.csr_of(el)
+    s = int(inputs.roots(el, 1, 22)[0])
+    level, parent, _ = oracle.bfs(g, s)
+    assert oracle.validate_edges(el.src, el.dst, el.n, s, level, parent).sum() == 0
+    reached = np.nonzero(level > 1)[0]
+    v = int(reached[0])
+    lv = level.copy(); lv[v] += 1                     # a level one too large
+    assert oracle.validate_edges(el.src, el.dst, el.n, s, lv, parent).sum() > 0
+    lv = level.copy(); lv[v] -= 1                     # a level one too small
+    assert oracle.validate_edges(el.src, el.dst, el.n, s, lv, parent).sum() > 0
+    cands = [u for u in g.row(v) if level[u] == level[v] - 1]
+    if len(cands) > 1:                                # a valid but non-maximal parent
+        pv = parent.copy(); pv[v] = min(cands)
+        assert oracle.validate_edges(el.src, el.dst, el.n, s, level, pv)[2] == 1
+    un = np.nonzero(level < 0)[0]
+    if un.size:                                        # an unreached vertex given a level
+        lv = level.copy(); lv[un[0]] = 3
+        assert oracle.validate_edges(el.src, el.dst, el.n, s, lv, parent).sum() > 0
+    pv = parent.copy(); pv[s] = -1                     # the source's own parent
+    assert oracle.validate_edges(el.src, el.dst, el.n, s, level, pv)[0] == 1
