@@ -363,6 +363,23 @@ def run_gpu(args, wl):
         comp["batched_gteps"] = round(sum(edges[:k]) / (bms / 1e3) / 1e9, 3)
         comp["batched_ms_per_64_roots"] = round(bms, 3)
         comp["plain_ms_per_64_roots"] = round(float(root_ms[:, :k].sum(axis=1).mean()), 3)
+        # autotuned: tuning picked on 8 other seeded roots, then all timed roots
+        if wl["kind"] == "rmat":
+            tune_roots = inputs.roots(el, 8, wl["root_seed"] + 7777)
+            tuned = bfs.bfs_autotune(g, tune_roots)
+            evt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in large]
+            for s in roots:
+                bfs.bfs_run(g, int(s), parent, level)
+            for (a, b), i in zip(evt, large):
+                a.record()
+                bfs.bfs_run(g, int(roots[i]), parent, level)
+                b.record()
+            torch.cuda.synchronize()
+            comp["autotuned_gteps"] = round(harmonic_gteps([edges[i] for i in large],
+                                                           [a.elapsed_time(b) / 1e3 for a, b in evt]), 3)
+            comp["autotuned"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuned.as_dict().items()}
+            bfs.bfs_set_tuning(g, **{f: 0 for f in ("warp_degree", "cta_degree", "pull_thread_degree",
+                                                     "chunk_degree", "batch_topdown_limit")}, alpha=0.0, beta=0.0)
         wpath = os.path.join(ROOT, "paper_1104_4518_gb300", "selector_weights.bin")
         if os.path.exists(wpath):
             bfs.bfs_selector_load(wpath)

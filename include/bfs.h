@@ -93,11 +93,11 @@ typedef struct bfs_tuning {
   int32_t warp_degree;   /* TD_BINNED: degree from which a vertex gets a warp (default 32) */
   int32_t cta_degree;    /* TD_BINNED: degree from which a vertex gets a CTA (default 256) */
   int32_t pull_thread_degree; /* PULL: top entries of a row each lane tests alone before the warp-wide scan
-                                 (1..8, default 4) */
+                                 (1..8, default 8) */
   int32_t chunk_degree;  /* top-down: vertices above this degree are split into grid-wide chunks of 1024
                             edges (>= 1024, default 1024) */
-  float alpha;           /* heuristic: go PULL when frontier edges > unvisited edges / alpha and the
-                            frontier grows (default 100) */
+  float alpha;           /* heuristic: go PULL when frontier edges * alpha' > unvisited edges and the
+                            frontier grows, alpha' = alpha * (1 + 4 n / L2 bytes) (default 30) */
   float beta;            /* heuristic: leave PULL when frontier count < n / beta (default 24) */
   int32_t batch_topdown_limit; /* batched: levels with at most this many active vertices expand top-down (default n/64) */
   int32_t reserved;

@@ -56,6 +56,9 @@ int current_device_info(DeviceInfo* out) {
     BFS_CUDA_TRY(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev));
     BFS_CUDA_TRY(cudaDeviceGetAttribute(&d.major, cudaDevAttrComputeCapabilityMajor, dev));
     BFS_CUDA_TRY(cudaDeviceGetAttribute(&d.minor, cudaDevAttrComputeCapabilityMinor, dev));
+    int l2 = 0;
+    BFS_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    d.l2_bytes = l2;
     int coop = 0;
     BFS_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (d.major * 10 + d.minor != 103 || !coop)
@@ -72,11 +75,11 @@ bfs_tuning effective_tuning(const bfs_graph* g) {
   if (t.warp_degree <= 0) t.warp_degree = 32;
   if (t.cta_degree <= 0) t.cta_degree = 256;
   if (t.cta_degree < t.warp_degree) t.cta_degree = t.warp_degree;
-  if (t.pull_thread_degree <= 0) t.pull_thread_degree = 4;
+  if (t.pull_thread_degree <= 0) t.pull_thread_degree = 8;
   if (t.pull_thread_degree > 8) t.pull_thread_degree = 8;
   if (t.chunk_degree <= 0) t.chunk_degree = 1024;
   if (t.chunk_degree < kChunkEdges) t.chunk_degree = kChunkEdges;
-  if (!(t.alpha > 0.0f)) t.alpha = 100.0f;
+  if (!(t.alpha > 0.0f)) t.alpha = 30.0f;
   if (!(t.beta > 0.0f)) t.beta = 24.0f;
   if (t.batch_topdown_limit <= 0) t.batch_topdown_limit = std::max(1024, g->n / 64);
   return t;
@@ -717,8 +720,8 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
     const int wd[] = {8, 16, 32, 64};
     const int cd[] = {128, 256, 1024};
     const int pd[] = {1, 2, 4, 6, 8};
-    const int ch[] = {1024, 4096, 16384};
-    const float al[] = {14.0f, 32.0f, 100.0f, 300.0f, 1000.0f};
+    const int ch[] = {1024, 2048, 4096};
+    const float al[] = {7.0f, 14.0f, 30.0f, 60.0f, 120.0f};
     const float be[] = {8.0f, 16.0f, 24.0f, 48.0f, 96.0f};
     for (int knob = 0; knob < 6 && !rc; ++knob) {
       const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 5 : knob == 3 ? 3 : 5;

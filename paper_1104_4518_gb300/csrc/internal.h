@@ -31,6 +31,7 @@ struct DeviceInfo {
   int device = -1;
   int sm_count = 0;
   int major = 0, minor = 0;
+  long long l2_bytes = 0;
 };
 int current_device_info(DeviceInfo* out);
 

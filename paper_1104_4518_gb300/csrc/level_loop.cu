@@ -173,16 +173,23 @@ __device__ __forceinline__ void td_visit(const LoopParams& p, const uint32_t* cu
 
 // Warp-cooperative descending scan of the rows still open in a warp: lane r
 // owns row r with entries [b, t) not yet examined (t exclusive, scanned from
-// t-1 down).  Every step the open rows' next entries are packed onto the 32
-// lanes by a prefix sum (at most 32 per row), each lane tests one entry
-// against the bitmap `bm`, and a row whose segment has a hit takes the hit of
-// its lowest lane (its highest position, i.e. its largest id) and closes.
-// All lanes call it; returns the row's hit or -1.
+// t-1 down).  Every step the open rows' next entries (at most kCoopRow per
+// row) are packed into kCoopSteps x 32 slots by a prefix sum; slot g is
+// examined by lane g % 32 in sub-step g / 32, so every lane has kCoopSteps
+// adjacency loads and bitmap loads in flight.  A row whose slots hold a hit
+// takes the hit in its lowest slot (its highest position, i.e. its largest
+// id) and closes.  All lanes call it; returns the row's hit or -1.
+#ifndef BFS_COOP_STEPS
+#define BFS_COOP_STEPS 1
+#endif
+constexpr int kCoopSteps = BFS_COOP_STEPS;
+constexpr int kCoopRow = 32 * kCoopSteps;
+
 __device__ __forceinline__ int scan_desc_coop(const int32_t* __restrict__ adj, const uint32_t* bm, long long b,
                                               long long t, bool open, int hit, int lane) {
   unsigned pm = __ballot_sync(kFull, open);
   while (pm) {
-    const int rc = open ? (int)min(t - b, 32ll) : 0;
+    const int rc = open ? (int)min(t - b, (long long)kCoopRow) : 0;
     int incl = rc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -191,30 +198,42 @@ __device__ __forceinline__ int scan_desc_coop(const int32_t* __restrict__ adj, c
     }
     const int excl = incl - rc;
     const int total = __shfl_sync(kFull, incl, 31);
-    // owner row of this lane's slot: the last row whose prefix is <= lane
-    int r = 0;
+    int u[kCoopSteps];
+    bool h[kCoopSteps];
 #pragma unroll
-    for (int st = 16; st >= 1; st >>= 1) {
-      const int c = r + st;
-      const int ec = __shfl_sync(kFull, excl, c & 31);
-      if (c < 32 && ec <= lane) r = c;
+    for (int sstep = 0; sstep < kCoopSteps; ++sstep) {
+      const int slot = sstep * 32 + lane;
+      // owner row of this slot: the last row whose prefix is <= slot
+      int r = 0;
+#pragma unroll
+      for (int st = 16; st >= 1; st >>= 1) {
+        const int c = r + st;
+        const int ec = __shfl_sync(kFull, excl, c & 31);
+        if (c < 32 && ec <= slot) r = c;
+      }
+      const long long tr = __shfl_sync(kFull, t, r);
+      const int er = __shfl_sync(kFull, excl, r);
+      u[sstep] = slot < total ? __ldg(&adj[tr - 1 - (slot - er)]) : -1;
     }
-    const long long tr = __shfl_sync(kFull, t, r);
-    const int er = __shfl_sync(kFull, excl, r);
-    int u = 0;
-    bool h = false;
-    if (lane < total) {
-      u = __ldg(&adj[tr - 1 - (lane - er)]);
-      h = (bm[u >> 5] >> (u & 31)) & 1u;
+#pragma unroll
+    for (int sstep = 0; sstep < kCoopSteps; ++sstep)
+      h[sstep] = u[sstep] >= 0 && ((bm[u[sstep] >> 5] >> (u[sstep] & 31)) & 1u);
+    // this lane's row takes slots [excl, excl + cons) of the kCoopRow slots
+    const int cons = max(0, min(rc, kCoopRow - excl));
+    int found = -1;
+#pragma unroll
+    for (int sstep = 0; sstep < kCoopSteps; ++sstep) {
+      const unsigned hm = __ballot_sync(kFull, h[sstep]);
+      const int lo = max(excl - sstep * 32, 0), hi = min(excl + cons - sstep * 32, 32);
+      unsigned seg = 0u;
+      if (hi > lo) seg = (hi - lo == 32 ? kFull : ((1u << (hi - lo)) - 1u)) << lo;
+      const unsigned mine = hm & seg;
+      const int hv = __shfl_sync(kFull, u[sstep], mine ? __ffs(mine) - 1 : 0);
+      if (found < 0 && mine) found = hv;
     }
-    const unsigned hm = __ballot_sync(kFull, h);
-    const int cons = max(0, min(rc, 32 - excl));
-    const unsigned seg = cons > 0 ? ((cons == 32 ? kFull : ((1u << cons) - 1u)) << excl) : 0u;
-    const unsigned mine = hm & seg;
-    const int hv = __shfl_sync(kFull, u, mine ? __ffs(mine) - 1 : 0);
     if (open) {
-      if (mine) {
-        hit = hv;
+      if (found >= 0) {
+        hit = found;
         open = false;
       } else {
         t -= cons;
@@ -445,6 +464,89 @@ __device__ __forceinline__ void warp_enqueue(const LoopParams& p, int knext, int
   nbuf = 0;
 }
 
+#ifdef BFS_PULL_PAIRS
+// Finishes one bitmap word of the pull phase: bitmap words, outputs, counters, queue.
+__device__ __forceinline__ void pull_finish(const LoopParams& p, uint32_t* nxt, long long ww, uint32_t vw,
+                                            uint32_t visw, int v, int hit, long long b, long long e, int knext,
+                                            Acc& acc, int* wq, int& nbuf, int lane) {
+  const unsigned hits = __ballot_sync(kFull, hit >= 0);
+  if (lane == 0) {
+    if (hits) nxt[ww] = hits;
+    if ((visw | hits) != vw) p.vis[ww] = visw | hits;
+  }
+  if (hit >= 0) {
+    p.parent[v] = hit;
+    p.level[v] = knext;
+    const long long deg = e - b;
+    acc_vertex(acc, deg);
+    if (deg > p.chunk_deg) push_chunks(p, knext, v, deg);
+  }
+  if (hits) warp_enqueue(p, knext, wq, nbuf, hit >= 0, v, lane, false);
+}
+
+// Two bitmap words per warp step: the offset, probe and bitmap loads of both
+// words are issued together, then each word's open rows get the warp scan.
+__device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
+  const uint32_t* cur = p.bits[k % 3];
+  uint32_t* nxt = p.bits[(k + 1) % 3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long gwarps = (long long)gridDim.x * kWarps;
+  const int knext = k + 1;
+  const int probe = min(p.pull_thread_deg, 4);
+  int* wq = sm.wq[wid];
+  int nbuf = 0;
+  for (long long w0 = ((long long)blockIdx.x * kBlock + threadIdx.x) / 32; w0 < p.nwords; w0 += 2 * gwarps) {
+    const long long w1 = w0 + gwarps;
+    const bool has1 = w1 < p.nwords;
+    const uint32_t vw0 = p.vis[w0], cw0 = cur[w0];
+    const uint32_t vw1 = has1 ? p.vis[w1] : 0xffffffffu, cw1 = has1 ? cur[w1] : 0u;
+    const uint32_t visw0 = vw0 | cw0, visw1 = vw1 | cw1;
+    if (lane == 0) {
+      if (visw0 == 0xffffffffu && vw0 != visw0) p.vis[w0] = visw0;
+      if (has1 && visw1 == 0xffffffffu && vw1 != visw1) p.vis[w1] = visw1;
+    }
+    const bool live0 = visw0 != 0xffffffffu, live1 = visw1 != 0xffffffffu;
+    if (!live0 && !live1) continue;
+    const int v0 = (int)(w0 * 32 + lane), v1 = (int)(w1 * 32 + lane);
+    const bool a0 = live0 && !((visw0 >> lane) & 1u), a1 = live1 && !((visw1 >> lane) & 1u);
+    long long b0 = 0, e0 = 0, b1 = 0, e1 = 0;
+    if (a0) {
+      b0 = __ldg(&p.off[v0]);
+      e0 = __ldg(&p.off[v0 + 1]);
+    }
+    if (a1) {
+      b1 = __ldg(&p.off[v1]);
+      e1 = __ldg(&p.off[v1 + 1]);
+    }
+    const int P0 = a0 ? (int)min((long long)probe, e0 - b0) : 0;
+    const int P1 = a1 ? (int)min((long long)probe, e1 - b1) : 0;
+    int u0[4], u1[4];
+    uint32_t x0[4], x1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      u0[q] = q < P0 ? __ldg(&p.adj[e0 - 1 - q]) : 0;
+      u1[q] = q < P1 ? __ldg(&p.adj[e1 - 1 - q]) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      x0[q] = q < P0 ? cur[u0[q] >> 5] : 0u;
+      x1[q] = q < P1 ? cur[u1[q] >> 5] : 0u;
+    }
+    int h0 = -1, h1 = -1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q < P0 && h0 < 0 && ((x0[q] >> (u0[q] & 31)) & 1u)) h0 = u0[q];
+      if (q < P1 && h1 < 0 && ((x1[q] >> (u1[q] & 31)) & 1u)) h1 = u1[q];
+    }
+    const long long t0 = e0 - P0, t1 = e1 - P1;
+    h0 = scan_desc_coop(p.adj, cur, b0, t0, a0 && h0 < 0 && t0 > b0, h0, lane);
+    h1 = scan_desc_coop(p.adj, cur, b1, t1, a1 && h1 < 0 && t1 > b1, h1, lane);
+    if (live0) pull_finish(p, nxt, w0, vw0, visw0, v0, h0, b0, e0, knext, acc, wq, nbuf, lane);
+    if (live1) pull_finish(p, nxt, w1, vw1, visw1, v1, h1, b1, e1, knext, acc, wq, nbuf, lane);
+  }
+  warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
+}
+#else
 __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
   const uint32_t* cur = p.bits[k % 3];
   uint32_t* nxt = p.bits[(k + 1) % 3];
@@ -504,9 +606,12 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
   warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
 }
 
+#endif  // BFS_PULL_PAIRS
+
 // Direction choice in the manner of direction-optimising BFS: go pull when the
 // frontier's edges exceed the unvisited edges / alpha while the frontier is
-// growing, leave pull when the frontier falls below n / beta.
+// growing, leave pull when the frontier falls below n / beta.  (p.alpha is the
+// tuned alpha scaled by 1 + 4 n / L2 bytes at launch.)
 __device__ __forceinline__ int heuristic_variant(const LoopParams& p, int prev_variant, long long count,
                                                  long long prev_count, long long edges,
                                                  long long unvisited_edges) {
@@ -623,26 +728,37 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
     } else if (p.selector == BFS_SELECT_SCHEDULE && k < p.schedule_len) {
       variant = p.schedule[k];
     } else if (learned) {
-      if (tid == 0) {
+      // the whole CTA evaluates the network (every CTA computes the same bits)
+      if (tid < 12) {
         const long long bins[3] = {(long long)__ldcg(&c->bins[0]), (long long)__ldcg(&c->bins[1]),
                                    (long long)__ldcg(&c->bins[2])};
-        bfsdev::level_features(p.n, p.nnz, k, count, edges, unvisited, unvisited_edges, bins, sm.x);
+        sm.x[tid] = bfsdev::level_feature(tid, p.n, p.nnz, k, count, edges, unvisited, unvisited_edges, bins);
       }
       __syncthreads();
       if (tid < 64) sm.h1[tid] = bfsdev::mlp_h1(s_mlp, sm.x, tid);
       __syncthreads();
-      if (tid < 64) sm.h2[tid] = bfsdev::mlp_h2(s_mlp, sm.h1, tid);
-      __syncthreads();
-      if (tid < 4) sm.y[tid] = bfsdev::mlp_out(s_mlp, sm.h2, tid);
-      __syncthreads();
-      if (tid == 0) {
-        int best = 0;
-        for (int o = 1; o < 4; ++o)
-          if (sm.y[o] < sm.y[best]) best = o;
-        sm.choice = best;
+      {  // layer 2: unit tid / 8, partial tid % 8, butterfly over the 8 lanes
+        const int t = tid >> 3;
+        float a = bfsdev::mlp_h2_part(s_mlp, sm.h1, t, tid & 7);
+        a = a + __shfl_xor_sync(kFull, a, 4);
+        a = a + __shfl_xor_sync(kFull, a, 2);
+        a = a + __shfl_xor_sync(kFull, a, 1);
+        if ((tid & 7) == 0) sm.h2[t] = fmaxf(a + s_mlp[bfsdev::kB2 + t], 0.0f);
       }
       __syncthreads();
-      variant = sm.choice;
+      if (tid < 128) {  // output layer: output tid / 32, partial tid % 32
+        const int o = tid >> 5;
+        float a = bfsdev::mlp_out_part(s_mlp, sm.h2, o, tid & 31);
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) a = a + __shfl_xor_sync(kFull, a, m);
+        if ((tid & 31) == 0) sm.y[o] = a + s_mlp[bfsdev::kB3 + o];
+      }
+      __syncthreads();
+      int best = 0;
+#pragma unroll
+      for (int o = 1; o < 4; ++o)
+        if (sm.y[o] < sm.y[best]) best = o;
+      variant = best;
     } else {
       variant = heuristic_variant(p, prev_variant, count, prev_count, edges, unvisited_edges);
     }
@@ -782,7 +898,9 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   p.cta_deg = t.cta_degree;
   p.pull_thread_deg = t.pull_thread_degree;
   p.chunk_deg = t.chunk_degree;
-  p.alpha = t.alpha;
+  // top-down's atomics on the parent array get dearer once 4 bytes per vertex
+  // no longer fit in L2, so the switch to pull comes earlier on large graphs
+  p.alpha = (float)(t.alpha * (1.0 + 4.0 * (double)g->n / (double)(di.l2_bytes > 0 ? di.l2_bytes : (1ll << 27))));
   p.beta = t.beta;
   p.parts = g->parts;
   p.part_base = g->d_part_base;

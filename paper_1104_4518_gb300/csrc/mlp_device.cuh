@@ -1,6 +1,8 @@
-// The selector network's forward pass for one input row, computed by a whole
-// CTA from shared memory.  Used by both the stand-alone forward kernel and the
-// in-loop variant selector, so that the two give bit-identical scores.
+// The selector network's forward pass.  The in-loop selector evaluates it with
+// a whole CTA (hidden layer 2 as 8 partial sums per unit combined by a
+// butterfly of shuffles, the output layer as 32 partial sums per output); the
+// stand-alone kernels evaluate the same sums in the same association order,
+// one thread per row, so both give bit-identical scores.
 #pragma once
 
 #include "bfs.h"
@@ -25,18 +27,65 @@ __device__ __forceinline__ float mlp_h1(const float* w, const float* x, int t) {
   return fmaxf(a, 0.0f);
 }
 
-__device__ __forceinline__ float mlp_h2(const float* w, const float* h1, int t) {
-  float a = w[kB2 + t];
-#pragma unroll 8
-  for (int i = 0; i < 64; ++i) a = fmaf(h1[i], w[kW2 + i * 64 + t], a);
-  return fmaxf(a, 0.0f);
+// Partial sum j (< 8) of hidden unit t of layer 2: inputs 8j .. 8j+7.
+__device__ __forceinline__ float mlp_h2_part(const float* w, const float* h1, int t, int j) {
+  float a = 0.0f;
+#pragma unroll
+  for (int i = 8 * j; i < 8 * j + 8; ++i) a = fmaf(h1[i], w[kW2 + i * 64 + t], a);
+  return a;
 }
 
+// Partial sum j (< 32) of output o: inputs j and j + 32.
+__device__ __forceinline__ float mlp_out_part(const float* w, const float* h2, int o, int j) {
+  return fmaf(h2[j + 32], w[kW3 + (j + 32) * 4 + o], h2[j] * w[kW3 + j * 4 + o]);
+}
+
+// Hidden unit t of layer 2, one thread: the 8 partial sums combined pairwise at
+// distance 4, 2, 1 (the order of a shuffle butterfly over 8 lanes).
+__device__ __forceinline__ float mlp_h2(const float* w, const float* h1, int t) {
+  float p[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) p[j] = mlp_h2_part(w, h1, t, j);
+#pragma unroll
+  for (int m = 4; m >= 1; m >>= 1)
+#pragma unroll
+    for (int j = 0; j < m; ++j) p[j] = p[j] + p[j + m];
+  return fmaxf(p[0] + w[kB2 + t], 0.0f);
+}
+
+// Output o, one thread: the 32 partial sums combined pairwise at distance 16 .. 1.
 __device__ __forceinline__ float mlp_out(const float* w, const float* h2, int o) {
-  float a = w[kB3 + o];
-#pragma unroll 8
-  for (int j = 0; j < 64; ++j) a = fmaf(h2[j], w[kW3 + j * 4 + o], a);
-  return a;
+  float p[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) p[j] = mlp_out_part(w, h2, o, j);
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+    for (int j = 0; j < m; ++j) p[j] = p[j] + p[j + m];
+  return p[0] + w[kB3 + o];
+}
+
+// Feature i (< 12) of a level (see bfs_level_features in bfs.h).
+__device__ __forceinline__ float level_feature(int i, int n, long long nnz, int k, long long count, long long edges,
+                                               long long unvisited, long long unvisited_edges,
+                                               const long long* bins) {
+  const float fn = (float)(n > 1 ? n : 1);
+  const float fe = (float)(nnz > 1 ? nnz : 1);
+  const float fc = (float)(count > 1 ? count : 1);
+  switch (i) {
+    case 0: return log2f(fn) / 32.0f;
+    case 1: return log2f(fe) / 32.0f;
+    case 2: return log2f(1.0f + (float)k) / 10.0f;
+    case 3: return log2f(1.0f + (float)count) / 32.0f;
+    case 4: return log2f(1.0f + (float)edges) / 32.0f;
+    case 5: return (float)count / fn;
+    case 6: return (float)edges / fe;
+    case 7: return (float)unvisited / fn;
+    case 8: return (float)unvisited_edges / fe;
+    case 9: return (float)bins[0] / fc;
+    case 10: return (float)bins[1] / fc;
+    default: return (float)bins[2] / fc;
+  }
 }
 
 // The 12 level features (see bfs_level_features in bfs.h).

@@ -136,3 +136,57 @@ def test_learned_selector_in_traversal():
                     assert x["variant"] == int(np.argmin(Yh[k]))
     finally:
         bfs.bfs_selector_set_params(None)
+
+
+def test_trained_selector_gain_over_the_heuristic():
+    """The committed, trained selector against the heuristic it replaces.
+
+    On an R-MAT graph outside the training set (scale 21, edgefactor 16, A = 0.57,
+    seed 99) and a 3D grid (80^3), the learned schedule must give identical
+    results, must not be slower than the heuristic by more than 10 % in total, and
+    must clearly beat a fixed variant (always top-down binned).  The measured
+    ratios are printed (pytest -s) as the gain of the network.
+    """
+    import os
+    path = os.path.join(os.path.dirname(bfs.__file__), "selector_weights.bin")
+    if not os.path.exists(path):
+        pytest.skip("no trained selector weights in the package")
+    bfs.bfs_selector_load(path)
+    try:
+        for el, roots in ((inputs.rmat(21, 16, seed=99), None), (inputs.grid3d(80), [0])):
+            if roots is None:
+                roots = [int(r) for r in inputs.roots(el, 8, 98)]
+            og = oracle.csr_of(el)
+            g = device_graph_from_edges(el)
+            n = g.n
+            par = torch.empty(n, dtype=torch.int32, device="cuda")
+            lev = torch.empty(n, dtype=torch.int32, device="cuda")
+
+            def total_ms(opts):
+                for s in roots:
+                    bfs.bfs_run(g, s, par, lev, opts)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                best = float("inf")
+                for _ in range(3):
+                    e0.record()
+                    for s in roots:
+                        bfs.bfs_run(g, s, par, lev, opts)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+                return best
+
+            learned = total_ms(bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED))
+            heur = total_ms(bfs.RunOptions(selector=bfs.BFS_SELECT_HEURISTIC))
+            fixed = total_ms(bfs.RunOptions(selector=bfs.BFS_SELECT_FORCED, forced_variant=bfs.BFS_VARIANT_TD_BINNED))
+            print(f"\n{el.name}: learned {learned:.3f} ms, heuristic {heur:.3f} ms "
+                  f"(gain x{heur / learned:.3f}), always top-down {fixed:.3f} ms (gain x{fixed / learned:.3f})")
+            for s in roots[:2]:
+                parent, level = bfs.run(g, s, bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED))
+                assert_same(oracle.bfs(og, s), (level.cpu().numpy(), parent.cpu().numpy()))
+            assert learned <= 1.10 * heur
+            assert learned < fixed
+            g.destroy()
+    finally:
+        bfs.bfs_selector_set_params(None)
