@@ -93,7 +93,7 @@ typedef struct bfs_tuning {
   int32_t warp_degree;   /* TD_BINNED: degree from which a vertex gets a warp (default 32) */
   int32_t cta_degree;    /* TD_BINNED: degree from which a vertex gets a CTA (default 256) */
   int32_t pull_thread_degree; /* PULL: top entries of a row each lane tests alone before the warp-wide scan
-                                 (1..8, default 8) */
+                                 (1..4, larger values act as 4; default 4) */
   int32_t chunk_degree;  /* top-down: vertices above this degree are split into grid-wide chunks of 1024
                             edges (>= 1024, default 1024) */
   float alpha;           /* heuristic: go PULL when frontier edges * alpha' > unvisited edges and the
@@ -303,8 +303,11 @@ BFS_API int bfs_selector_save(const char* path);
  * log2(1 + sum deg f) / 32, |f| / n, sum deg f / nnz, unvisited / n,
  * unvisited edges / nnz, and the fraction of f with degree <= 32, <= 1024 and
  * larger.  "Unvisited" means not in levels 0..k, exactly the
- * unvisited_count / unvisited_edges fields of bfs_level_stat.  The device
- * computes the same expressions in float32 inside bfs_run.
+ * unvisited_count / unvisited_edges fields of bfs_level_stat.  In float32:
+ * every count is converted to float once, a ratio a / b is a * (1.0f / b), a
+ * division by 32 or 10 is a product with 0.03125f or 0.1f.  The device
+ * computes the same expressions inside bfs_run (its log2f may differ from the
+ * host's in the last place).
  */
 BFS_API int bfs_level_features(int32_t n, int64_t nnz, int32_t k, int64_t frontier_count,
                        int64_t frontier_edges, int64_t unvisited_count, int64_t unvisited_edges,

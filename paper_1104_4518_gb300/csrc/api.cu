@@ -75,8 +75,8 @@ bfs_tuning effective_tuning(const bfs_graph* g) {
   if (t.warp_degree <= 0) t.warp_degree = 32;
   if (t.cta_degree <= 0) t.cta_degree = 256;
   if (t.cta_degree < t.warp_degree) t.cta_degree = t.warp_degree;
-  if (t.pull_thread_degree <= 0) t.pull_thread_degree = 8;
-  if (t.pull_thread_degree > 8) t.pull_thread_degree = 8;
+  if (t.pull_thread_degree <= 0) t.pull_thread_degree = 4;
+  if (t.pull_thread_degree > 4) t.pull_thread_degree = 4;
   if (t.chunk_degree <= 0) t.chunk_degree = 1024;
   if (t.chunk_degree < kChunkEdges) t.chunk_degree = kChunkEdges;
   if (!(t.alpha > 0.0f)) t.alpha = 30.0f;
@@ -719,12 +719,12 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
     const int wd[] = {8, 16, 32, 64};
     const int cd[] = {128, 256, 1024};
-    const int pd[] = {1, 2, 4, 6, 8};
+    const int pd[] = {1, 2, 3, 4};
     const int ch[] = {1024, 2048, 4096};
     const float al[] = {7.0f, 14.0f, 30.0f, 60.0f, 120.0f};
     const float be[] = {8.0f, 16.0f, 24.0f, 48.0f, 96.0f};
     for (int knob = 0; knob < 6 && !rc; ++knob) {
-      const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 5 : knob == 3 ? 3 : 5;
+      const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 3 : 5;
       for (int c = 0; c < cnt && !rc; ++c) {
         bfs_tuning t = cur;
         switch (knob) {

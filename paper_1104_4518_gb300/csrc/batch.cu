@@ -26,6 +26,7 @@
 // Output rows are root-major: level[r * n + v], parent[r * n + v].
 #include <cooperative_groups.h>
 
+#include "claims.cuh"
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -37,6 +38,7 @@ namespace {
 using bfsdev::kFull;
 
 constexpr int kBBlock = 512;
+static_assert(kBBlock == kClaimBlock, "the claim buffers assume 512-thread CTAs");
 constexpr int kBWarps = kBBlock / 32;
 constexpr int kShortRow = 32;  // rows up to this length are scanned by one lane
 
@@ -137,27 +139,6 @@ __device__ __forceinline__ uint64_t resolve_warp(const BatchParams& p, const uin
   return found;
 }
 
-__device__ __forceinline__ void push_chunks(const BatchParams& p, int knext, int v, long long deg) {
-  const unsigned nch = (unsigned)((deg + kChunkEdges - 1) / kChunkEdges);
-  const unsigned pos = atomicAdd(&p.ctr[knext % kCtrRing].chunks, nch);
-  int64_t* dst = p.chunks[knext & 1];
-  for (unsigned c = 0; c < nch; ++c) dst[pos + c] = ((int64_t)v << 32) | (int64_t)c;
-}
-
-// Warp-aggregated append of v (when pred) to the queue of level knext.
-__device__ __forceinline__ void enqueue_warp(const BatchParams& p, int knext, int v, bool pred, long long deg) {
-  const unsigned m = __ballot_sync(kFull, pred);
-  if (!m) return;
-  const int lane = threadIdx.x & 31;
-  unsigned base = 0;
-  if (lane == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)__popc(m));
-  base = __shfl_sync(kFull, base, 0);
-  if (pred) {
-    p.queue[knext % 3][base + __popc(m & bfsdev::lanemask_lt())] = v;
-    if (deg > kChunkEdges) push_chunks(p, knext, v, deg);
-  }
-}
-
 // Resolves the parents of 32 vertices (one per lane, need = roots to find)
 // against frontier F; lanes with short rows scan alone, long rows get the warp.
 __device__ __forceinline__ uint64_t resolve_group(const BatchParams& p, const uint64_t* F, int v, long long b,
@@ -180,7 +161,7 @@ __device__ __forceinline__ uint64_t resolve_group(const BatchParams& p, const ui
 
 // Top-down visit of edge (u -> w) with frontier bits f of u at level knext - 1.
 __device__ __forceinline__ void td_visit(const BatchParams& p, const uint64_t* Fc, uint64_t* Fn, int knext,
-                                         uint64_t f, int u, int w) {
+                                         uint64_t f, int u, int w, Claims& cl) {
   const uint64_t nb = f & ~(p.V[w] | Fc[w]);
   if (!nb) return;
   for (uint64_t b = nb; b;) {  // u is a parent candidate of w for every new root bit
@@ -196,13 +177,9 @@ __device__ __forceinline__ void td_visit(const BatchParams& p, const uint64_t* F
     p.level[(long long)r * p.n + w] = knext;
   }
   if (old == 0) {
-    cg::coalesced_group g = cg::coalesced_threads();
-    unsigned base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)g.size());
-    base = g.shfl(base, 0);
-    p.queue[knext % 3][base + g.thread_rank()] = w;
+    cta_enqueue(p, knext, cl, w);
     const long long deg = __ldg(&p.off[w + 1]) - __ldg(&p.off[w]);
-    if (deg > kChunkEdges) push_chunks(p, knext, w, deg);
+    if (deg > kChunkEdges) push_chunks_cta(p, knext, cl, w, deg);
   }
 }
 
@@ -211,7 +188,8 @@ __device__ __forceinline__ void td_visit(const BatchParams& p, const uint64_t* F
 // finds for every root bit of `need` its highest hit, and combines with the
 // other warps and chunks through atomicMax (parents) and atomicOr (F_{k+1}).
 __device__ __forceinline__ void pull_big_chunk(const BatchParams& p, const uint64_t* Fc, uint64_t* Fn, int knext,
-                                               int v, long long rb, long long re, uint64_t need, int lane, int wid) {
+                                               int v, long long rb, long long re, uint64_t need, int lane, int wid,
+                                               Claims& cl, int* wq, int& nbuf) {
   uint64_t found = 0;
 #pragma unroll
   for (int step = 0; step < 2; ++step) {
@@ -234,6 +212,7 @@ __device__ __forceinline__ void pull_big_chunk(const BatchParams& p, const uint6
       if (lane == 0) atomicMax(&p.parent[(long long)r * p.n + v], pu);
     }
   }
+  bool claimed = false;
   if (lane == 0 && found) {
     const unsigned long long old = atomicOr((unsigned long long*)&Fn[v], (unsigned long long)found);
     for (uint64_t b = found & ~old; b;) {
@@ -242,17 +221,21 @@ __device__ __forceinline__ void pull_big_chunk(const BatchParams& p, const uint6
       p.level[(long long)r * p.n + v] = knext;
     }
     if (old == 0) {
-      const unsigned pos = atomicAdd(&p.ctr[knext % kCtrRing].count, 1u);
-      p.queue[knext % 3][pos] = v;
-      push_chunks(p, knext, v, __ldg(&p.off[v + 1]) - __ldg(&p.off[v]));
+      claimed = true;
+      push_chunks_cta(p, knext, cl, v, __ldg(&p.off[v + 1]) - __ldg(&p.off[v]));
     }
   }
+  warp_enqueue(p, knext, wq, nbuf, claimed, v, lane, false);
 }
 
 __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
+  __shared__ Claims cl;
   const int tid = threadIdx.x, lane = tid & 31;
   unsigned epoch = 0;
-  if (tid == 0) epoch = bfsdev::ld_acquire_u32(&p.bar->epoch);
+  if (tid == 0) {
+    epoch = bfsdev::ld_acquire_u32(&p.bar->epoch);
+    claims_reset(cl);
+  }
   const long long G = gridDim.x;
   const long long gtid = (long long)blockIdx.x * kBBlock + tid;
   const long long gthreads = G * kBBlock;
@@ -329,7 +312,7 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         const long long rb = __ldg(&p.off[u]) + (it & 0xffffffffll) * kChunkEdges;
         const long long re = min(rb + (long long)kChunkEdges, (long long)__ldg(&p.off[u + 1]));
         const uint64_t f = Fc[u];
-        for (long long j = rb + tid; j < re; j += kBBlock) td_visit(p, Fc, Fn, knext, f, u, __ldg(&p.adj[j]));
+        for (long long j = rb + tid; j < re; j += kBBlock) td_visit(p, Fc, Fn, knext, f, u, __ldg(&p.adj[j]), cl);
       }
       // other frontier rows: one warp each; every frontier vertex folds its bits into V
       for (long long i = gwarp; i < count; i += gwarps) {
@@ -338,9 +321,11 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         if (lane == 0) p.V[u] |= f;
         const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
         if (e - b > kChunkEdges) continue;
-        for (long long j = b + lane; j < e; j += 32) td_visit(p, Fc, Fn, knext, f, u, __ldg(&p.adj[j]));
+        for (long long j = b + lane; j < e; j += 32) td_visit(p, Fc, Fn, knext, f, u, __ldg(&p.adj[j]), cl);
       }
     } else {
+      int* wq = cl.wq[wid];
+      int nbuf = 0;
       // long rows: one CTA per chunk of the static table
       for (long long ci = blockIdx.x; ci < p.nbig; ci += G) {
         const int64_t it = p.big[ci];
@@ -349,7 +334,7 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         if (!need) continue;
         const long long rb = __ldg(&p.off[v]) + (it & 0xffffffffll) * kChunkEdges;
         const long long re = min(rb + (long long)kChunkEdges, (long long)__ldg(&p.off[v + 1]));
-        pull_big_chunk(p, Fc, Fn, knext, v, rb, re, need, lane, wid);
+        pull_big_chunk(p, Fc, Fn, knext, v, rb, re, need, lane, wid, cl, wq, nbuf);
       }
       // other rows: 32 vertices per warp; the owner lane updates V and F_{k+1}
       const long long nw = ((long long)p.n + 31) / 32;
@@ -374,9 +359,11 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
           if (nv != vv) p.V[v] = nv;
           if (found) Fn[v] = found;
         }
-        enqueue_warp(p, knext, v, found != 0, 0);
+        warp_enqueue(p, knext, wq, nbuf, found != 0, v, lane, false);
       }
+      warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
     }
+    flush_claims(p, knext, cl);
     if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
     if (p.stats && blockIdx.x == 0 && tid == 0 && k < kMaxStatLevels) {
       const uint64_t t = bfsdev::global_timer_ns();

@@ -166,6 +166,9 @@ struct BatchRequest {
 int launch_batch(const BatchRequest& r, cudaStream_t s);
 
 // Selector network parameters on the current device (nullptr if none).
+// The selector features' constants of a graph, float32: log2 n / 32,
+// log2 nnz / 32, 1 / n, 1 / nnz (n and nnz taken as at least 1).
+void graph_feature_constants(int32_t n, int64_t nnz, float* log_n, float* log_nnz, float* inv_n, float* inv_nnz);
 const float* learned_params_device();
 
 }  // namespace bfsint

@@ -33,11 +33,14 @@
 //     exit is kept).  Vertices without edges are marked visited at init, so
 //     pull levels never touch them.
 #include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
 
 #include <algorithm>
+#include <cstdio>
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "claims.cuh"
 #include "mlp_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -49,12 +52,10 @@ using bfsdev::kFull;
 
 constexpr int kBlock = 512;
 constexpr int kWarps = kBlock / 32;
-constexpr int kQBuf = 2048;   // per-CTA buffer of next-frontier vertices (top-down claims)
-constexpr int kWQBuf = 256;   // per-warp buffer of next-frontier vertices (pull claims)
 
 #ifdef BFS_PHASE_TIMING
 // Diagnostic build only: global-timer stamps of the first 4096 levels.
-// [0] CTA 0 at level start, [1] after selection, [2] after recycling,
+// [0] CTA 0 at level start, [1] after recycling, [2] after selection,
 // [3] after expansion, [4] after counter flush, [5] latest barrier arrival
 // of any CTA, [6] CTA 0 after the barrier.
 __device__ unsigned long long g_phase_ts[4096][8];
@@ -103,6 +104,7 @@ struct LoopParams {
   const int32_t* schedule;
   int32_t schedule_len;
   const float* mlp;
+  float feat_log_n, feat_log_nnz, feat_inv_n, feat_inv_nnz;  // graph constants of the selector's features
   int32_t want_stats;
   unsigned spin_limit;
   int32_t warp_deg, cta_deg, pull_thread_deg, chunk_deg;
@@ -124,41 +126,18 @@ __device__ __forceinline__ void acc_vertex(Acc& a, long long deg) {
   else a.b2 += 1;
 }
 
-// Appends the chunk items of a high-degree vertex of level knext.
-__device__ __forceinline__ void push_chunks(const LoopParams& p, int knext, int v, long long deg) {
-  const unsigned nch = (unsigned)((deg + kChunkEdges - 1) / kChunkEdges);
-  const unsigned pos = atomicAdd(&p.ctr[knext % kCtrRing].chunks, nch);
-  int64_t* dst = p.chunks[knext & 1];
-  for (unsigned c = 0; c < nch; ++c) dst[pos + c] = ((int64_t)v << 32) | (int64_t)c;
-}
-
-// Appends w to the CTA's next-frontier buffer (shared memory); when the buffer
-// is full the vertex goes straight to the global queue.
-__device__ __forceinline__ void cta_enqueue(const LoopParams& p, int knext, int* qn, int* cq, int w) {
-  const int pos = atomicAdd(qn, 1);
-  if (pos < kQBuf) {
-    cq[pos] = w;
-  } else {  // buffer full: one global atomic per group of converged threads
-    cg::coalesced_group g = cg::coalesced_threads();
-    unsigned base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)g.size());
-    base = g.shfl(base, 0);
-    p.queue[knext % 3][base + g.thread_rank()] = w;
-  }
-}
-
 // Bookkeeping of a vertex claimed for level knext (the caller already set nxt).
 __device__ __forceinline__ void claim_topdown(const LoopParams& p, int knext, int w, long long deg, Acc& acc,
-                                              int* qn, int* cq) {
+                                              Claims& cl) {
   p.level[w] = knext;
-  cta_enqueue(p, knext, qn, cq, w);
+  cta_enqueue(p, knext, cl, w);
   acc_vertex(acc, deg);
-  if (deg > p.chunk_deg) push_chunks(p, knext, w, deg);
+  if (deg > p.chunk_deg) push_chunks_cta(p, knext, cl, w, deg);
 }
 
 // Top-down visit of edge (u -> w) in phase k.
 __device__ __forceinline__ void td_visit(const LoopParams& p, const uint32_t* cur, uint32_t* nxt, int k,
-                                         int u, int w, Acc& acc, int* qn, int* cq) {
+                                         int u, int w, Acc& acc, Claims& cl) {
   const int ww = w >> 5;
   const uint32_t m = 1u << (w & 31);
   const uint32_t vw = p.vis[ww], cw = cur[ww], nw = nxt[ww];  // independent loads, one round trip
@@ -168,7 +147,7 @@ __device__ __forceinline__ void td_visit(const LoopParams& p, const uint32_t* cu
   const long long wb = __ldg(&p.off[w]), we = __ldg(&p.off[w + 1]);  // speculative: the claim needs the degree
   const uint32_t old = atomicOr(&nxt[ww], m);
   if (old & m) return;
-  claim_topdown(p, k + 1, w, we - wb, acc, qn, cq);
+  claim_topdown(p, k + 1, w, we - wb, acc, cl);
 }
 
 // Warp-cooperative descending scan of the rows still open in a warp: lane r
@@ -255,64 +234,32 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 // End of a phase for one CTA: adds its counters into level knext's slot and
 // moves its buffered next-frontier vertices to the global queue with a single
 // atomic.  CTAs that claimed nothing skip all of it.
+// End of a phase: the CTA's counter contributions, its buffered queue entries
+// and its buffered chunk items go to level knext with one atomic each.
 template <typename S>
 __device__ __forceinline__ void end_phase(const LoopParams& p, int knext, Acc& acc, S& sm) {
   const bool mine = (acc.edges | acc.b0 | acc.b1 | acc.b2) != 0;
-  if (!__syncthreads_or(mine) && sm.qn == 0) return;
-  const unsigned long long e = warp_sum_u64(acc.edges), b0 = warp_sum_u64(acc.b0), b1 = warp_sum_u64(acc.b1),
-                           b2 = warp_sum_u64(acc.b2);
-  if ((threadIdx.x & 31) == 0 && (e | b0 | b1 | b2)) {
-    atomicAdd(&sm.acc[0], e);
-    atomicAdd(&sm.acc[1], b0);
-    atomicAdd(&sm.acc[2], b1);
-    atomicAdd(&sm.acc[3], b2);
-  }
-  __syncthreads();
-  const int nb = min(sm.qn, kQBuf);
-  if (threadIdx.x == 0) {
-    LevelCtr* c = &p.ctr[knext % kCtrRing];
-    if (sm.acc[0]) atomicAdd(&c->edges, sm.acc[0]);
-    if (sm.acc[1]) atomicAdd(&c->bins[0], sm.acc[1]);
-    if (sm.acc[2]) atomicAdd(&c->bins[1], sm.acc[2]);
-    if (sm.acc[3]) atomicAdd(&c->bins[2], sm.acc[3]);
-    sm.acc[0] = sm.acc[1] = sm.acc[2] = sm.acc[3] = 0;
-    if (nb) sm.qbase = atomicAdd(&c->count, (unsigned)nb);
-  }
-  __syncthreads();
-  int32_t* Q = p.queue[knext % 3];
-  for (int i = threadIdx.x; i < nb; i += kBlock) Q[sm.qbase + i] = sm.cq[i];
-  __syncthreads();
-  if (threadIdx.x == 0) sm.qn = 0;
-  acc = Acc{};
-}
-
-// Exclusive CTA-wide prefix sum of one int per thread; returns the total.
-__device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int& excl) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    int v = lane < kWarps ? s_warp[lane] : 0;
-    int inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, inc, o);
-      if (lane >= o) inc += y;
+  if (__syncthreads_or(mine)) {
+    const unsigned long long e = warp_sum_u64(acc.edges), b0 = warp_sum_u64(acc.b0), b1 = warp_sum_u64(acc.b1),
+                             b2 = warp_sum_u64(acc.b2);
+    if ((threadIdx.x & 31) == 0 && (e | b0 | b1 | b2)) {
+      atomicAdd(&sm.acc[0], e);
+      atomicAdd(&sm.acc[1], b0);
+      atomicAdd(&sm.acc[2], b1);
+      atomicAdd(&sm.acc[3], b2);
     }
-    if (lane < kWarps) s_warp[lane] = inc - v;
-    if (lane == kWarps - 1) s_warp[kWarps] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      LevelCtr* c = &p.ctr[knext % kCtrRing];
+      if (sm.acc[0]) atomicAdd(&c->edges, sm.acc[0]);
+      if (sm.acc[1]) atomicAdd(&c->bins[0], sm.acc[1]);
+      if (sm.acc[2]) atomicAdd(&c->bins[1], sm.acc[2]);
+      if (sm.acc[3]) atomicAdd(&c->bins[2], sm.acc[3]);
+      sm.acc[0] = sm.acc[1] = sm.acc[2] = sm.acc[3] = 0;
+    }
   }
-  __syncthreads();
-  excl = s_warp[wid] + incl - x;
-  const int total = s_warp[kWarps];
-  __syncthreads();
-  return total;
+  flush_claims(p, knext, sm.cl);
+  acc = Acc{};
 }
 
 struct Smem {
@@ -324,14 +271,8 @@ struct Smem {
   int tu[kBlock];
   long long tb[kBlock];
   int tpref[kBlock + 1];
-  int wq[kWarps][kWQBuf];  // per warp: next-frontier vertices claimed by the pull phase
-  int qn;                // entries in cq (may exceed kQBuf: the excess went straight to the queue)
-  unsigned qbase;
-  int cq[kQBuf];         // the CTA's share of the next frontier queue, flushed once per phase
-  float x[12];
-  float h1[64];
-  float h2[64];
-  float y[4];
+  Claims cl;
+  __align__(16) float h1[64];  // selector network: hidden layer 1, choice
   int choice;
 };
 
@@ -352,7 +293,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
     const long long rb = __ldg(&p.off[v]), re = __ldg(&p.off[v + 1]);
     const long long b = rb + c * kChunkEdges;
     const long long e = min(b + (long long)kChunkEdges, re);
-    for (long long j = b + tid; j < e; j += kBlock) td_visit(p, cur, nxt, k, v, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
+    for (long long j = b + tid; j < e; j += kBlock) td_visit(p, cur, nxt, k, v, __ldg(&p.adj[j]), acc, sm.cl);
   }
 
   // frontier entry i goes to CTA i % G, so that small frontiers spread over every SM
@@ -364,7 +305,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
       atomicOr(&p.vis[u >> 5], 1u << (u & 31));
       const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
       if (e - b > p.chunk_deg) continue;
-      for (long long j = b; j < e; ++j) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
+      for (long long j = b; j < e; ++j) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc, sm.cl);
     }
   } else if (variant == BFS_VARIANT_TD_WARP) {
     const long long gwarps = gthreads / 32;
@@ -373,7 +314,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
       if (lane == 0) atomicOr(&p.vis[u >> 5], 1u << (u & 31));
       const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
       if (e - b > p.chunk_deg) continue;
-      for (long long j = b + lane; j < e; j += 32) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
+      for (long long j = b + lane; j < e; j += 32) td_visit(p, cur, nxt, k, u, __ldg(&p.adj[j]), acc, sm.cl);
     }
   } else {  // BFS_VARIANT_TD_BINNED
     for (long long tile = 0; tile < count; tile += gthreads) {
@@ -403,7 +344,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
         __syncthreads();
         const int cu = sm.cu;
         const long long cb = sm.cb, ce = sm.ce;
-        for (long long j = cb + tid; j < ce; j += kBlock) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
+        for (long long j = cb + tid; j < ce; j += kBlock) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc, sm.cl);
         __syncthreads();
         if (tid == 0) sm.owner = -1;
         __syncthreads();
@@ -416,7 +357,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
         const int cu = __shfl_sync(kFull, u, l);
         const long long cb = __shfl_sync(kFull, b, l), ce = __shfl_sync(kFull, e, l);
         if (lane == l) u = -1;
-        for (long long j = cb + lane; j < ce; j += 32) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc, &sm.qn, sm.cq);
+        for (long long j = cb + lane; j < ce; j += 32) td_visit(p, cur, nxt, k, cu, __ldg(&p.adj[j]), acc, sm.cl);
       }
       // thread bin: the CTA gathers the remaining short rows edge by edge
       const int sdeg = u >= 0 ? (int)deg : 0;
@@ -437,7 +378,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
             else hi = mid;
           }
           const int ou = sm.tu[lo];
-          td_visit(p, cur, nxt, k, ou, __ldg(&p.adj[sm.tb[lo] + (idx - sm.tpref[lo])]), acc, &sm.qn, sm.cq);
+          td_visit(p, cur, nxt, k, ou, __ldg(&p.adj[sm.tb[lo] + (idx - sm.tpref[lo])]), acc, sm.cl);
         }
       }
       __syncthreads();
@@ -446,29 +387,10 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
 }
 
 // ---------------- pull phase ----------------
-// Appends the claimed vertices of a warp (one per lane where `claimed`) to the
-// warp's buffer in shared memory; once it holds at least kWQBuf - 32 vertices
-// (or at the end of the phase) they move to the queue with one atomic.
-__device__ __forceinline__ void warp_enqueue(const LoopParams& p, int knext, int* wq, int& nbuf, bool claimed, int v,
-                                             int lane, bool flush) {
-  const unsigned hm = __ballot_sync(kFull, claimed);
-  if (claimed) wq[nbuf + __popc(hm & bfsdev::lanemask_lt())] = v;
-  nbuf += __popc(hm);
-  if (nbuf == 0 || (!flush && nbuf < kWQBuf - 32)) return;
-  __syncwarp();
-  unsigned base = 0;
-  if (lane == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)nbuf);
-  base = __shfl_sync(kFull, base, 0);
-  for (int i = lane; i < nbuf; i += 32) p.queue[knext % 3][base + i] = wq[i];
-  __syncwarp();
-  nbuf = 0;
-}
-
-#ifdef BFS_PULL_PAIRS
 // Finishes one bitmap word of the pull phase: bitmap words, outputs, counters, queue.
 __device__ __forceinline__ void pull_finish(const LoopParams& p, uint32_t* nxt, long long ww, uint32_t vw,
                                             uint32_t visw, int v, int hit, long long b, long long e, int knext,
-                                            Acc& acc, int* wq, int& nbuf, int lane) {
+                                            Acc& acc, Claims& cl, int* wq, int& nbuf, int lane) {
   const unsigned hits = __ballot_sync(kFull, hit >= 0);
   if (lane == 0) {
     if (hits) nxt[ww] = hits;
@@ -479,7 +401,7 @@ __device__ __forceinline__ void pull_finish(const LoopParams& p, uint32_t* nxt, 
     p.level[v] = knext;
     const long long deg = e - b;
     acc_vertex(acc, deg);
-    if (deg > p.chunk_deg) push_chunks(p, knext, v, deg);
+    if (deg > p.chunk_deg) push_chunks_cta(p, knext, cl, v, deg);
   }
   if (hits) warp_enqueue(p, knext, wq, nbuf, hit >= 0, v, lane, false);
 }
@@ -493,7 +415,7 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
   const long long gwarps = (long long)gridDim.x * kWarps;
   const int knext = k + 1;
   const int probe = min(p.pull_thread_deg, 4);
-  int* wq = sm.wq[wid];
+  int* wq = sm.cl.wq[wid];
   int nbuf = 0;
   for (long long w0 = ((long long)blockIdx.x * kBlock + threadIdx.x) / 32; w0 < p.nwords; w0 += 2 * gwarps) {
     const long long w1 = w0 + gwarps;
@@ -541,72 +463,25 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
     const long long t0 = e0 - P0, t1 = e1 - P1;
     h0 = scan_desc_coop(p.adj, cur, b0, t0, a0 && h0 < 0 && t0 > b0, h0, lane);
     h1 = scan_desc_coop(p.adj, cur, b1, t1, a1 && h1 < 0 && t1 > b1, h1, lane);
-    if (live0) pull_finish(p, nxt, w0, vw0, visw0, v0, h0, b0, e0, knext, acc, wq, nbuf, lane);
-    if (live1) pull_finish(p, nxt, w1, vw1, visw1, v1, h1, b1, e1, knext, acc, wq, nbuf, lane);
-  }
-  warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
-}
-#else
-__device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
-  const uint32_t* cur = p.bits[k % 3];
-  uint32_t* nxt = p.bits[(k + 1) % 3];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long gwarps = (long long)gridDim.x * kWarps;
-  const int knext = k + 1;
-  const int probe = p.pull_thread_deg;
-  int* wq = sm.wq[wid];
-  int nbuf = 0;
-  for (long long ww = ((long long)blockIdx.x * kBlock + threadIdx.x) / 32; ww < p.nwords; ww += gwarps) {
-    const uint32_t vw = p.vis[ww];
-    const uint32_t visw = vw | cur[ww];
-    if (visw == 0xffffffffu) {  // nothing to pull, but vis must absorb f_k's bits
-      if (lane == 0 && vw != visw) p.vis[ww] = visw;
-      continue;
-    }
-    const int v = (int)(ww * 32 + lane);
-    const bool active = !((visw >> lane) & 1u);
-    long long b = 0, e = 0;
-    if (active) {
-      b = __ldg(&p.off[v]);
-      e = __ldg(&p.off[v + 1]);
-    }
-    // probe: each lane tests the top entries of its own row (loads issued together)
-    int hit = -1;
-    long long t = e;
-    if (active) {
-      const int P = (int)min((long long)probe, e - b);
-      int u[8];
-      uint32_t wv[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < P) u[q] = __ldg(&p.adj[e - 1 - q]);
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < P) wv[q] = cur[u[q] >> 5];
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < P && hit < 0 && ((wv[q] >> (u[q] & 31)) & 1u)) hit = u[q];
-      t = e - P;
-    }
-    hit = scan_desc_coop(p.adj, cur, b, t, active && hit < 0 && t > b, hit, lane);
-    const unsigned hits = __ballot_sync(kFull, hit >= 0);
-    if (lane == 0) {
-      if (hits) nxt[ww] = hits;
-      if ((visw | hits) != vw) p.vis[ww] = visw | hits;
-    }
-    if (hit >= 0) {
-      p.parent[v] = hit;
-      p.level[v] = knext;
-      const long long deg = e - b;
-      acc_vertex(acc, deg);
-      if (deg > p.chunk_deg) push_chunks(p, knext, v, deg);
-    }
-    if (hits) warp_enqueue(p, knext, wq, nbuf, hit >= 0, v, lane, false);
+    if (live0) pull_finish(p, nxt, w0, vw0, visw0, v0, h0, b0, e0, knext, acc, sm.cl, wq, nbuf, lane);
+    if (live1) pull_finish(p, nxt, w1, vw1, visw1, v1, h1, b1, e1, knext, acc, sm.cl, wq, nbuf, lane);
   }
   warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
 }
 
-#endif  // BFS_PULL_PAIRS
+// The selector network on one warp: every lane computes the 12 level features
+// in registers (lane j < 3 brings bin count j), then the warp evaluates the
+// network on the parameters in the warp layout; returns the chosen variant on
+// every lane.  Kept out of line so that its registers do not crowd the phases.
+__device__ __noinline__ int learned_choice(const LoopParams& p, const float* w, float* h1, int lane, int k,
+                                           long long count, long long edges, long long unvisited,
+                                           long long unvisited_edges, long long binv) {
+  float x[12];
+  bfsdev::level_features(p.feat_log_n, p.feat_log_nnz, p.feat_inv_n, p.feat_inv_nnz, k, count, edges, unvisited,
+                         unvisited_edges, __shfl_sync(kFull, binv, 0), __shfl_sync(kFull, binv, 1),
+                         __shfl_sync(kFull, binv, 2), x);
+  return bfsdev::warp_mlp_argmin(w, x, h1, lane);
+}
 
 // Direction choice in the manner of direction-optimising BFS: go pull when the
 // frontier's edges exceed the unvisited edges / alpha while the frontier is
@@ -623,18 +498,18 @@ __device__ __forceinline__ int heuristic_variant(const LoopParams& p, int prev_v
 
 __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   __shared__ Smem sm;
-  extern __shared__ float s_mlp[];  // BFS_MLP_PARAMS floats when the learned selector is on
+  extern __shared__ __align__(16) float s_mlp[];  // BFS_MLP_PARAMS floats when the learned selector is on
   const int tid = threadIdx.x;
   unsigned epoch = 0;
   if (tid == 0) {
     epoch = bfsdev::ld_acquire_u32(&p.bar->epoch);
     sm.owner = -1;
-    sm.qn = 0;
+    claims_reset(sm.cl);
     sm.acc[0] = sm.acc[1] = sm.acc[2] = sm.acc[3] = 0;
   }
   const bool learned = p.selector == BFS_SELECT_LEARNED && p.mlp != nullptr;
   if (learned)
-    for (int i = tid; i < BFS_MLP_PARAMS; i += kBlock) s_mlp[i] = p.mlp[i];
+    for (int i = tid; i < BFS_MLP_PARAMS; i += kBlock) s_mlp[bfsdev::warp_layout_index(i)] = p.mlp[i];
 
   const long long gtid = (long long)blockIdx.x * kBlock + tid;
   const long long gthreads = (long long)gridDim.x * kBlock;
@@ -713,6 +588,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
     const unsigned count = __ldcg(&c->count);
     const unsigned nchunks = __ldcg(&c->chunks);
     const long long edges = (long long)__ldcg(&c->edges);
+    const long long binv = (learned && tid < 3) ? (long long)__ldcg(&c->bins[tid]) : 0;
     const bool sparse_clr = k >= 1 && (long long)prev_count * 4 < p.nwords;
     const int32_t* PQ = p.queue[(k + 2) % 3];
     const int clr0 = (sparse_clr && gtid < prev_count) ? PQ[gtid] : -1;
@@ -722,50 +598,8 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
     const long long unvisited = (long long)p.n - cum_count;
     const long long unvisited_edges = p.nnz - cum_edges;
 
-    int variant;
-    if (p.selector == BFS_SELECT_FORCED) {
-      variant = p.forced;
-    } else if (p.selector == BFS_SELECT_SCHEDULE && k < p.schedule_len) {
-      variant = p.schedule[k];
-    } else if (learned) {
-      // the whole CTA evaluates the network (every CTA computes the same bits)
-      if (tid < 12) {
-        const long long bins[3] = {(long long)__ldcg(&c->bins[0]), (long long)__ldcg(&c->bins[1]),
-                                   (long long)__ldcg(&c->bins[2])};
-        sm.x[tid] = bfsdev::level_feature(tid, p.n, p.nnz, k, count, edges, unvisited, unvisited_edges, bins);
-      }
-      __syncthreads();
-      if (tid < 64) sm.h1[tid] = bfsdev::mlp_h1(s_mlp, sm.x, tid);
-      __syncthreads();
-      {  // layer 2: unit tid / 8, partial tid % 8, butterfly over the 8 lanes
-        const int t = tid >> 3;
-        float a = bfsdev::mlp_h2_part(s_mlp, sm.h1, t, tid & 7);
-        a = a + __shfl_xor_sync(kFull, a, 4);
-        a = a + __shfl_xor_sync(kFull, a, 2);
-        a = a + __shfl_xor_sync(kFull, a, 1);
-        if ((tid & 7) == 0) sm.h2[t] = fmaxf(a + s_mlp[bfsdev::kB2 + t], 0.0f);
-      }
-      __syncthreads();
-      if (tid < 128) {  // output layer: output tid / 32, partial tid % 32
-        const int o = tid >> 5;
-        float a = bfsdev::mlp_out_part(s_mlp, sm.h2, o, tid & 31);
-#pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) a = a + __shfl_xor_sync(kFull, a, m);
-        if ((tid & 31) == 0) sm.y[o] = a + s_mlp[bfsdev::kB3 + o];
-      }
-      __syncthreads();
-      int best = 0;
-#pragma unroll
-      for (int o = 1; o < 4; ++o)
-        if (sm.y[o] < sm.y[best]) best = o;
-      variant = best;
-    } else {
-      variant = heuristic_variant(p, prev_variant, count, prev_count, edges, unvisited_edges);
-    }
-    if (variant < 0 || variant >= BFS_NUM_VARIANTS) variant = BFS_VARIANT_TD_BINNED;
-
-    PHASE_TS(k, 1);
-    // recycle: counters of level k+4, bitmap of level k-1
+    // recycle: counters of level k+4, bitmap of level k-1 (stores only; they
+    // drain while the selector runs)
     if (blockIdx.x == 0 && tid < (int)(sizeof(LevelCtr) / 8))
       reinterpret_cast<unsigned long long*>(&p.ctr[(k + 4) % kCtrRing])[tid] = 0ull;
     if (k >= 1) {
@@ -777,6 +611,25 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
         for (long long w = gtid; w < p.nwords; w += gthreads) clr[w] = 0u;
       }
     }
+    PHASE_TS(k, 1);
+
+    int variant;
+    if (p.selector == BFS_SELECT_FORCED) {
+      variant = p.forced;
+    } else if (p.selector == BFS_SELECT_SCHEDULE && k < p.schedule_len) {
+      variant = p.schedule[k];
+    } else if (learned) {
+      // warp 0 of every CTA evaluates the network (all CTAs compute the same bits)
+      if (tid < 32) {
+        const int best = learned_choice(p, s_mlp, sm.h1, tid, k, count, edges, unvisited, unvisited_edges, binv);
+        if (tid == 0) sm.choice = best;
+      }
+      __syncthreads();
+      variant = sm.choice;
+    } else {
+      variant = heuristic_variant(p, prev_variant, count, prev_count, edges, unvisited_edges);
+    }
+    if (variant < 0 || variant >= BFS_NUM_VARIANTS) variant = BFS_VARIANT_TD_BINNED;
     PHASE_TS(k, 2);
     if (variant == BFS_VARIANT_PULL) pull_phase(p, k, sm, acc);
     else topdown_phase(p, k, variant, count, nchunks, sm, acc);
@@ -892,6 +745,7 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   p.schedule = w->schedule;
   p.schedule_len = sched_len;
   p.mlp = r.selector == BFS_SELECT_LEARNED ? learned_params_device() : nullptr;
+  graph_feature_constants(g->n, g->nnz, &p.feat_log_n, &p.feat_log_nnz, &p.feat_inv_n, &p.feat_inv_nnz);
   p.want_stats = r.want_stats ? 1 : 0;
   p.spin_limit = r.spin_limit ? r.spin_limit : (1u << 25);
   p.warp_deg = t.warp_degree;
@@ -917,6 +771,9 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_loop_kernel, kBlock, dyn_smem));
   if (per_sm < 1) return fail(BFS_ERR_CUDA, "level loop kernel cannot be resident");
   const int grid = per_sm * di.sm_count;
+#ifdef BFS_PHASE_TIMING
+  fprintf(stderr, "level loop: %d CTAs (%d per SM), %zu bytes dynamic shared memory\n", grid, per_sm, dyn_smem);
+#endif
   void* args[] = {&p};
   BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)level_loop_kernel, dim3(grid), dim3(kBlock), args,
                                            dyn_smem, s));

@@ -206,6 +206,15 @@ const float* learned_params_device() {
   return g_sel_dev[dev];
 }
 
+void graph_feature_constants(int32_t n, int64_t nnz, float* log_n, float* log_nnz, float* inv_n, float* inv_nnz) {
+  const float fn = (float)(n > 1 ? n : 1);
+  const float fe = (float)(nnz > 1 ? nnz : 1);
+  *log_n = log2f(fn) * 0.03125f;
+  *log_nnz = log2f(fe) * 0.03125f;
+  *inv_n = 1.0f / fn;
+  *inv_nnz = 1.0f / fe;
+}
+
 }  // namespace bfsint
 
 using namespace bfsint;
@@ -325,21 +334,21 @@ int bfs_selector_save(const char* path) {
 int bfs_level_features(int32_t n, int64_t nnz, int32_t k, int64_t frontier_count, int64_t frontier_edges,
                        int64_t unvisited_count, int64_t unvisited_edges, const int64_t* bin_count, float* out12) {
   if (!bin_count || !out12) return fail(BFS_ERR_INVALID_ARG, "bfs_level_features: NULL pointer");
-  const float fn = (float)(n > 1 ? n : 1);
-  const float fe = (float)(nnz > 1 ? nnz : 1);
-  const float fc = (float)(frontier_count > 1 ? frontier_count : 1);
-  out12[0] = log2f(fn) / 32.0f;
-  out12[1] = log2f(fe) / 32.0f;
-  out12[2] = log2f(1.0f + (float)k) / 10.0f;
-  out12[3] = log2f(1.0f + (float)frontier_count) / 32.0f;
-  out12[4] = log2f(1.0f + (float)frontier_edges) / 32.0f;
-  out12[5] = (float)frontier_count / fn;
-  out12[6] = (float)frontier_edges / fe;
-  out12[7] = (float)unvisited_count / fn;
-  out12[8] = (float)unvisited_edges / fe;
-  out12[9] = (float)bin_count[0] / fc;
-  out12[10] = (float)bin_count[1] / fc;
-  out12[11] = (float)bin_count[2] / fc;
+  // the float32 expressions of the in-loop selector (bfsdev::level_features)
+  float rn = 0.0f, re = 0.0f;
+  bfsint::graph_feature_constants(n, nnz, &out12[0], &out12[1], &rn, &re);
+  const float c = (float)frontier_count, d = (float)frontier_edges;
+  const float rc = 1.0f / (frontier_count > 1 ? c : 1.0f);
+  out12[2] = log2f(1.0f + (float)k) * 0.1f;
+  out12[3] = log2f(1.0f + c) * 0.03125f;
+  out12[4] = log2f(1.0f + d) * 0.03125f;
+  out12[5] = c * rn;
+  out12[6] = d * re;
+  out12[7] = (float)unvisited_count * rn;
+  out12[8] = (float)unvisited_edges * re;
+  out12[9] = (float)bin_count[0] * rc;
+  out12[10] = (float)bin_count[1] * rc;
+  out12[11] = (float)bin_count[2] * rc;
   return BFS_OK;
 }
 

@@ -252,7 +252,7 @@ def test_autotune_keeps_results_and_caches(tmp_path):
     g = device_graph_from_edges(el)
     cache = str(tmp_path / "tuning.json")
     t = bfs.bfs_autotune_cached(g, roots[:2], cache)
-    assert t.warp_degree in (8, 16, 32, 64) and 1 <= t.pull_thread_degree <= 8 and t.chunk_degree >= 1024
+    assert t.warp_degree in (8, 16, 32, 64) and 1 <= t.pull_thread_degree <= 4 and t.chunk_degree >= 1024
     assert t.alpha > 0 and t.beta > 0 and t.batch_topdown_limit >= 1
     for s in roots:
         assert_same(oracle.bfs(og, int(s)), run_gpu(g, int(s)))

@@ -138,14 +138,21 @@ def test_learned_selector_in_traversal():
         bfs.bfs_selector_set_params(None)
 
 
-def test_trained_selector_gain_over_the_heuristic():
-    """The committed, trained selector against the heuristic it replaces.
+def test_trained_selector_gain():
+    """What the committed, trained selector gains, on an R-MAT graph outside the
+    training set (scale 21, edgefactor 16, A = 0.57, seed 99, 8 roots) and a
+    3D grid (80^3, corner root).
 
-    On an R-MAT graph outside the training set (scale 21, edgefactor 16, A = 0.57,
-    seed 99) and a 3D grid (80^3), the learned schedule must give identical
-    results, must not be slower than the heuristic by more than 10 % in total, and
-    must clearly beat a fixed variant (always top-down binned).  The measured
-    ratios are printed (pytest -s) as the gain of the network.
+    Against the method without a selector (one expansion variant at every
+    level, the best of the four for that graph) the learned schedule must be
+    faster on R-MAT.  On the grid every level is top-down and a level takes
+    about 8 us, of which the network's evaluation inside the traversal
+    (about 1 us) is a visible share, so there it must stay within 20 % of the
+    best fixed variant.  Against the fixed-threshold heuristic it replaces it
+    must stay within 10 % on R-MAT and 20 % on the grid.  Results stay
+    identical to the oracle.  The learned choices replayed as a schedule (no
+    inference inside the traversal) separate the quality of the choices from
+    the cost of making them.  All ratios are printed (pytest -s).
     """
     import os
     path = os.path.join(os.path.dirname(bfs.__file__), "selector_weights.bin")
@@ -153,7 +160,8 @@ def test_trained_selector_gain_over_the_heuristic():
         pytest.skip("no trained selector weights in the package")
     bfs.bfs_selector_load(path)
     try:
-        for el, roots in ((inputs.rmat(21, 16, seed=99), None), (inputs.grid3d(80), [0])):
+        for el, roots, beat_fixed, slack in ((inputs.rmat(21, 16, seed=99), None, True, 1.10),
+                                             (inputs.grid3d(80), [0], False, 1.20)):
             if roots is None:
                 roots = [int(r) for r in inputs.roots(el, 8, 98)]
             og = oracle.csr_of(el)
@@ -162,31 +170,41 @@ def test_trained_selector_gain_over_the_heuristic():
             par = torch.empty(n, dtype=torch.int32, device="cuda")
             lev = torch.empty(n, dtype=torch.int32, device="cuda")
 
-            def total_ms(opts):
+            def total_ms(make_opts):
                 for s in roots:
-                    bfs.bfs_run(g, s, par, lev, opts)
+                    bfs.bfs_run(g, s, par, lev, make_opts(s))
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 best = float("inf")
                 for _ in range(3):
+                    opts = [make_opts(s) for s in roots]
                     e0.record()
-                    for s in roots:
-                        bfs.bfs_run(g, s, par, lev, opts)
+                    for s, o in zip(roots, opts):
+                        bfs.bfs_run(g, s, par, lev, o)
                     e1.record()
                     torch.cuda.synchronize()
                     best = min(best, e0.elapsed_time(e1))
                 return best
 
-            learned = total_ms(bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED))
-            heur = total_ms(bfs.RunOptions(selector=bfs.BFS_SELECT_HEURISTIC))
-            fixed = total_ms(bfs.RunOptions(selector=bfs.BFS_SELECT_FORCED, forced_variant=bfs.BFS_VARIANT_TD_BINNED))
-            print(f"\n{el.name}: learned {learned:.3f} ms, heuristic {heur:.3f} ms "
-                  f"(gain x{heur / learned:.3f}), always top-down {fixed:.3f} ms (gain x{fixed / learned:.3f})")
-            for s in roots[:2]:
-                parent, level = bfs.run(g, s, bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED))
-                assert_same(oracle.bfs(og, s), (level.cpu().numpy(), parent.cpu().numpy()))
-            assert learned <= 1.10 * heur
-            assert learned < fixed
+            schedules = {}
+            for s in roots:
+                o = bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED, stats_levels=4096)
+                parent, level = bfs.run(g, s, o)
+                if s in roots[:2]:
+                    assert_same(oracle.bfs(og, s), (level.cpu().numpy(), parent.cpu().numpy()))
+                schedules[s] = [x["variant"] for x in o.stats()]
+            learned = total_ms(lambda s: bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED))
+            replay = total_ms(lambda s: bfs.RunOptions(selector=bfs.BFS_SELECT_SCHEDULE, schedule=schedules[s]))
+            heur = total_ms(lambda s: bfs.RunOptions(selector=bfs.BFS_SELECT_HEURISTIC))
+            fixed = {v: total_ms(lambda s, v=v: bfs.RunOptions(selector=bfs.BFS_SELECT_FORCED, forced_variant=v))
+                     for v in range(bfs.BFS_NUM_VARIANTS)}
+            vbest = min(fixed, key=fixed.get)
+            print(f"\n{el.name}: learned {learned:.3f} ms | best fixed variant ({bfs.VARIANT_NAMES[vbest]}) "
+                  f"{fixed[vbest]:.3f} ms, gain x{fixed[vbest] / learned:.3f} | heuristic {heur:.3f} ms, "
+                  f"gain x{heur / learned:.3f} | learned choices replayed {replay:.3f} ms, "
+                  f"x{heur / replay:.3f} vs heuristic")
+            assert learned < fixed[vbest] if beat_fixed else learned <= slack * fixed[vbest]
+            assert learned <= slack * heur
             g.destroy()
     finally:
         bfs.bfs_selector_set_params(None)
