@@ -173,11 +173,7 @@ def profile_traffic(name: str):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
-    src = os.path.join(ROOT, "paper_1104_4518_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in ("level_loop.cu", "device_common.cuh", "internal.h", "mlp_device.cuh"):
-        h.update(open(os.path.join(src, f), "rb").read())
-    if kv.get("source_sha256") != h.hexdigest()[:16]:
+    if kv.get("source_sha256") != kernel_source_hash():
         return None
     try:
         return float(kv["traffic_bytes_per_launch"])
@@ -190,7 +186,7 @@ def kernel_source_hash() -> str:
 
     src = os.path.join(ROOT, "paper_1104_4518_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("level_loop.cu", "device_common.cuh", "internal.h", "mlp_device.cuh"):
+    for f in ("level_loop.cu", "claims.cuh", "device_common.cuh", "internal.h", "mlp_device.cuh"):
         h.update(open(os.path.join(src, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -379,7 +375,8 @@ def run_gpu(args, wl):
                                                            [a.elapsed_time(b) / 1e3 for a, b in evt]), 3)
             comp["autotuned"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuned.as_dict().items()}
             bfs.bfs_set_tuning(g, **{f: 0 for f in ("warp_degree", "cta_degree", "pull_thread_degree",
-                                                     "chunk_degree", "batch_topdown_limit")}, alpha=0.0, beta=0.0)
+                                                     "chunk_degree", "batch_topdown_limit", "small_frontier")},
+                               alpha=0.0, beta=0.0)
         wpath = os.path.join(ROOT, "paper_1104_4518_gb300", "selector_weights.bin")
         if os.path.exists(wpath):
             bfs.bfs_selector_load(wpath)

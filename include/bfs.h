@@ -100,7 +100,9 @@ typedef struct bfs_tuning {
                             frontier grows, alpha' = alpha * (1 + 4 n / L2 bytes) (default 30) */
   float beta;            /* heuristic: leave PULL when frontier count < n / beta (default 24) */
   int32_t batch_topdown_limit; /* batched: levels with at most this many active vertices expand top-down (default n/64) */
-  int32_t reserved;
+  int32_t small_frontier; /* heuristic: a top-down level whose frontier has at most this many vertices, none of
+                             degree above 32, runs TD_WARP instead of TD_BINNED (0 = default: the warps resident
+                             in the traversal's grid; negative = never) */
 } bfs_tuning;
 
 /* Options of one run (NULL = heuristic selector, no statistics). */
@@ -238,8 +240,10 @@ BFS_API int bfs_get_tuning(const bfs_graph* g, bfs_tuning* t);
 
 /*
  * Times bfs_run over `nroots` host roots (ids) for a small grid of tuning
- * candidates (bin degrees, pull thread degree, chunk degree, heuristic alpha and
- * beta), keeps the fastest as the graph's tuning and copies it to *best.
+ * candidates (bin degrees, pull thread degree, chunk degree, heuristic alpha,
+ * beta and small_frontier; coordinate descent, two sweeps), then
+ * bfs_run_batch over the first 64 of them for the batched top-down limit; keeps
+ * the fastest as the graph's tuning and copies it to *best.
  * Synchronises the stream; results never change, only speed.
  */
 BFS_API int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning* best, void* stream);

@@ -723,8 +723,9 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
     const int ch[] = {1024, 2048, 4096};
     const float al[] = {7.0f, 14.0f, 30.0f, 60.0f, 120.0f};
     const float be[] = {8.0f, 16.0f, 24.0f, 48.0f, 96.0f};
-    for (int knob = 0; knob < 6 && !rc; ++knob) {
-      const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 3 : 5;
+    const int sf[] = {-1, 0, 2 * 4864, 4 * 4864};
+    for (int knob = 0; knob < 7 && !rc; ++knob) {
+      const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 3 : knob == 6 ? 4 : 5;
       for (int c = 0; c < cnt && !rc; ++c) {
         bfs_tuning t = cur;
         switch (knob) {
@@ -733,7 +734,8 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
           case 2: t.pull_thread_degree = pd[c]; break;
           case 3: t.chunk_degree = ch[c]; break;
           case 4: t.alpha = al[c]; break;
-          default: t.beta = be[c]; break;
+          case 5: t.beta = be[c]; break;
+          default: t.small_frontier = sf[c]; break;
         }
         float ms = 0.0f;
         rc = time_plain(t, &ms);

@@ -109,6 +109,7 @@ struct LoopParams {
   unsigned spin_limit;
   int32_t warp_deg, cta_deg, pull_thread_deg, chunk_deg;
   float alpha, beta;
+  long long small_frontier;  // TD_WARP for top-down levels up to this many vertices, all of degree <= 32
   int32_t parts;
   const int64_t* part_base;
   int32_t** part_out;  // [2 * parts]: level outputs then parent outputs
@@ -489,11 +490,13 @@ __device__ __noinline__ int learned_choice(const LoopParams& p, const float* w, 
 // tuned alpha scaled by 1 + 4 n / L2 bytes at launch.)
 __device__ __forceinline__ int heuristic_variant(const LoopParams& p, int prev_variant, long long count,
                                                  long long prev_count, long long edges,
-                                                 long long unvisited_edges) {
+                                                 long long unvisited_edges, bool small_rows) {
   bool pull;
   if (prev_variant == BFS_VARIANT_PULL) pull = (float)count * p.beta >= (float)p.n;
   else pull = (float)edges * p.alpha > (float)unvisited_edges && count >= prev_count;
-  return pull ? BFS_VARIANT_PULL : BFS_VARIANT_TD_BINNED;
+  if (pull) return BFS_VARIANT_PULL;
+  // a small frontier of short rows: one warp per vertex beats the binning's scan
+  return (count <= p.small_frontier && small_rows) ? BFS_VARIANT_TD_WARP : BFS_VARIANT_TD_BINNED;
 }
 
 __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
@@ -589,6 +592,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
     const unsigned nchunks = __ldcg(&c->chunks);
     const long long edges = (long long)__ldcg(&c->edges);
     const long long binv = (learned && tid < 3) ? (long long)__ldcg(&c->bins[tid]) : 0;
+    const unsigned long long big_rows = __ldcg(&c->bins[1]) | __ldcg(&c->bins[2]);
     const bool sparse_clr = k >= 1 && (long long)prev_count * 4 < p.nwords;
     const int32_t* PQ = p.queue[(k + 2) % 3];
     const int clr0 = (sparse_clr && gtid < prev_count) ? PQ[gtid] : -1;
@@ -627,7 +631,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
       __syncthreads();
       variant = sm.choice;
     } else {
-      variant = heuristic_variant(p, prev_variant, count, prev_count, edges, unvisited_edges);
+      variant = heuristic_variant(p, prev_variant, count, prev_count, edges, unvisited_edges, big_rows == 0);
     }
     if (variant < 0 || variant >= BFS_NUM_VARIANTS) variant = BFS_VARIANT_TD_BINNED;
     PHASE_TS(k, 2);
@@ -771,6 +775,7 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_loop_kernel, kBlock, dyn_smem));
   if (per_sm < 1) return fail(BFS_ERR_CUDA, "level loop kernel cannot be resident");
   const int grid = per_sm * di.sm_count;
+  p.small_frontier = t.small_frontier > 0 ? t.small_frontier : (t.small_frontier == 0 ? (long long)grid * kWarps : 0);
 #ifdef BFS_PHASE_TIMING
   fprintf(stderr, "level loop: %d CTAs (%d per SM), %zu bytes dynamic shared memory\n", grid, per_sm, dyn_smem);
 #endif
