@@ -375,8 +375,8 @@ def run_gpu(args, wl):
                                                            [a.elapsed_time(b) / 1e3 for a, b in evt]), 3)
             comp["autotuned"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuned.as_dict().items()}
             bfs.bfs_set_tuning(g, **{f: 0 for f in ("warp_degree", "cta_degree", "pull_thread_degree",
-                                                     "chunk_degree", "batch_topdown_limit", "small_frontier")},
-                               alpha=0.0, beta=0.0)
+                                                     "chunk_degree", "batch_topdown_limit", "small_frontier",
+                                                     "batch_width")}, alpha=0.0, beta=0.0)
         wpath = os.path.join(ROOT, "paper_1104_4518_gb300", "selector_weights.bin")
         if os.path.exists(wpath):
             bfs.bfs_selector_load(wpath)

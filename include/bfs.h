@@ -103,6 +103,9 @@ typedef struct bfs_tuning {
   int32_t small_frontier; /* heuristic: a top-down level whose frontier has at most this many vertices, none of
                              degree above 32, runs TD_WARP instead of TD_BINNED (0 = default: the warps resident
                              in the traversal's grid; negative = never) */
+  int32_t batch_width;   /* batched: roots per traversal, the bits of a frontier word: 8, 16, 32 or 64
+                            (default 64) */
+  int32_t reserved;
 } bfs_tuning;
 
 /* Options of one run (NULL = heuristic selector, no statistics). */
@@ -181,11 +184,12 @@ BFS_API int bfs_run(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* 
 
 /*
  * BFS from k sources at once: outputs are root-major int32[k][n] (row i belongs
- * to sources[i], a host array).  Up to 64 roots share one traversal in which
- * every vertex carries 64-bit frontier and visited bitsets (a boolean sparse
+ * to sources[i], a host array).  Up to W roots share one traversal in which
+ * every vertex carries W-bit frontier and visited bitsets (a boolean sparse
  * matrix-dense matrix product per level); parents follow the same max-id rule,
  * recovered by scanning each newly reached vertex's row from the largest id
- * down.  k > 64 runs in chunks of 64.  Results equal k calls of bfs_run.
+ * down.  W = bfs_tuning.batch_width (8, 16, 32 or 64, default 64); k > W
+ * runs in chunks of W.  Results equal k calls of bfs_run.
  * Each level expands top-down when its frontier has at most
  * bfs_tuning.batch_topdown_limit vertices, by pull otherwise.  With
  * opts->stats, the levels of the last chunk are reported (frontier_count,

@@ -82,6 +82,7 @@ bfs_tuning effective_tuning(const bfs_graph* g) {
   if (!(t.alpha > 0.0f)) t.alpha = 30.0f;
   if (!(t.beta > 0.0f)) t.beta = 24.0f;
   if (t.batch_topdown_limit <= 0) t.batch_topdown_limit = std::max(1024, g->n / 64);
+  if (t.batch_width != 8 && t.batch_width != 16 && t.batch_width != 32 && t.batch_width != 64) t.batch_width = 64;
   return t;
 }
 
@@ -90,7 +91,7 @@ void free_workspace(Workspace* w) {
   void* ptrs[] = {w->queue[0], w->queue[1], w->queue[2], w->queue[3], w->bits[0], w->bits[1], w->bits[2],
                   w->bits[3], w->vis, w->chunks[0], w->chunks[1], w->ctr, w->barrier, w->status, w->stats, w->misc,
                   w->edges_out, w->schedule, w->sources, w->tmp_level, w->tmp_parent, w->bset[0], w->bset[1],
-                  w->bset[2], w->bvis, w->part_out};
+                  w->bset[2], w->bvis, w->bscr, w->part_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (w->h_stage) cudaFreeHost(w->h_stage);
@@ -159,6 +160,8 @@ int ensure_batch_state(bfs_graph* g, Workspace* w) {
   for (int i = 0; i < 3; ++i)
     if (int e = dev_alloc((void**)&w->bset[i], n8, "batch frontier bitsets")) return e;
   if (int e = dev_alloc((void**)&w->bvis, n8, "batch visited bitsets")) return e;
+  if (int e = dev_alloc((void**)&w->bscr, sizeof(int32_t) * 2 * 64 * (size_t)g->n, "batch scratch results"))
+    return e;
   return BFS_OK;
 }
 
@@ -502,16 +505,18 @@ int bfs_run_batch(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* pare
     dp = dl + n * 64;
   }
   int rc = BFS_OK;
-  for (int c = 0; c < k && !rc; c += 64) {
+  const int width = effective_tuning(g).batch_width;
+  for (int c = 0; c < k && !rc; c += width) {
     BatchRequest br;
     br.g = g;
     br.w = w;
     br.h_sources = sources + c;
-    br.k = std::min(64, k - c);
+    br.k = std::min(width, k - c);
+    br.width = width;
     br.level = host ? dl : level_out + (size_t)c * n;
     br.parent = host ? dp : parent_out + (size_t)c * n;
     br.spin_limit = opts ? opts->spin_limit : 0;
-    br.want_stats = opts && opts->stats && c + 64 >= k;  // statistics of the last chunk
+    br.want_stats = opts && opts->stats && c + width >= k;  // statistics of the last chunk
     rc = launch_batch(br, s);
     if (!rc && host) {
       cudaError_t err = cudaMemcpyAsync(level_out + (size_t)c * n, dl, sizeof(int32_t) * n * br.k,
@@ -753,6 +758,16 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
     for (int c = 0; c < 5 && !rc; ++c) {
       bfs_tuning t = cur;
       t.batch_topdown_limit = std::max(1, (int)(g->n * fr[c]));
+      float ms = 0.0f;
+      rc = time_batch(t, &ms);
+      if (!rc && ms < bms) {
+        bms = ms;
+        cur = t;
+      }
+    }
+    for (int wbits = 8; wbits <= 64 && kb == 64 && !rc; wbits *= 2) {  // roots per traversal (64 roots timed)
+      bfs_tuning t = cur;
+      t.batch_width = wbits;
       float ms = 0.0f;
       rc = time_batch(t, &ms);
       if (!rc && ms < bms) {

@@ -23,7 +23,17 @@
 //              largest id wins); the first writer of a root bit writes the
 //              level, the first writer of any bit enqueues the neighbour.
 //              Rows above kChunkEdges entries are split into chunk items.
-// Output rows are root-major: level[r * n + v], parent[r * n + v].
+// Output rows are root-major: level[r * n + v], parent[r * n + v].  During
+// the traversal the results go to vertex-major scratch (sl / sp [v][r], one
+// row of `stride` ints per vertex), so that the results of one vertex share a
+// few sectors instead of landing 4 * n bytes apart; a last phase transposes the
+// scratch into the outputs through shared-memory tiles, coalesced both ways.
+//
+// The words are 8, 16, 32 or 64 bits wide (one bit per root of the
+// traversal; bit arithmetic is done in 64-bit registers whatever the word).
+// 64 is the default: a traversal's row scans cost about the same whatever
+// the number of roots it carries, so fewer, wider traversals win even when
+// the frontier array no longer fits in L2 (measured at scales 22 to 26).
 #include <cooperative_groups.h>
 
 #include "claims.cuh"
@@ -52,8 +62,11 @@ struct BatchParams {
   int32_t src[64];
   int32_t* level;   // [k][n]
   int32_t* parent;  // [k][n]
-  uint64_t* F[3];
-  uint64_t* V;
+  int32_t* sl;      // scratch levels [n][stride]
+  int32_t* sp;      // scratch parents [n][stride]
+  int32_t stride;   // roots per scratch row (the word width)
+  void* F[3];  // Word[n] each
+  void* V;     // Word[n]
   int32_t* queue[3];
   int64_t* chunks[2];
   const int64_t* big;  // chunks of rows longer than kChunkEdges (static, per graph)
@@ -67,20 +80,50 @@ struct BatchParams {
   long long td_limit;
 };
 
+using Bits = unsigned long long;
+
+// atomicOr of v into a word of an 8-, 16-, 32- or 64-bit array; returns the old word.
+template <typename Word>
+__device__ __forceinline__ Bits atomic_or_word(Word* a, Bits v) {
+  if constexpr (sizeof(Word) == 8) {
+    return atomicOr(reinterpret_cast<unsigned long long*>(a), v);
+  } else if constexpr (sizeof(Word) == 4) {
+    return atomicOr(reinterpret_cast<unsigned*>(a), (unsigned)v);
+  } else {  // the aligned 32-bit word that holds *a
+    const uintptr_t ad = reinterpret_cast<uintptr_t>(a);
+    const int sh = (int)(ad & 3u) * 8;
+    const unsigned old = atomicOr(reinterpret_cast<unsigned*>(ad & ~(uintptr_t)3), (unsigned)v << sh);
+    return (Bits)((old >> sh) & ((1u << (8 * sizeof(Word))) - 1u));
+  }
+}
+
+// OR of v over the warp (v has at most 8 * sizeof(Word) bits).
+template <typename Word>
+__device__ __forceinline__ Bits warp_or(Bits v) {
+  const unsigned lo = __reduce_or_sync(kFull, (unsigned)v);
+  if constexpr (sizeof(Word) == 8) {
+    const unsigned hi = __reduce_or_sync(kFull, (unsigned)(v >> 32));
+    return ((Bits)hi << 32) | lo;
+  } else {
+    return lo;
+  }
+}
+
 // Writes level / parent of the roots in `bits` for vertex v.
 __device__ __forceinline__ void write_hits(const BatchParams& p, uint64_t bits, int v, int u, int lvl) {
   while (bits) {
     const int r = __ffsll((long long)bits) - 1;
     bits &= bits - 1;
-    const long long o = (long long)r * p.n + v;
-    p.level[o] = lvl;
-    p.parent[o] = u;
+    const long long o = (long long)v * p.stride + r;
+    p.sl[o] = lvl;
+    p.sp[o] = u;
   }
 }
 
 // One lane scans rows [b, e) of v from the top, four loads at a time, and
 // resolves the roots in `need`; returns the bits found.
-__device__ __forceinline__ uint64_t resolve_lane(const BatchParams& p, const uint64_t* F, int v, long long b,
+template <typename Word>
+__device__ __forceinline__ uint64_t resolve_lane(const BatchParams& p, const Word* F, int v, long long b,
                                                  long long e, uint64_t need, int lvl) {
   uint64_t found = 0;
   long long j = e - 1;
@@ -90,7 +133,7 @@ __device__ __forceinline__ uint64_t resolve_lane(const BatchParams& p, const uin
 #pragma unroll
     for (int q = 0; q < 4; ++q) u[q] = (j - q >= b) ? __ldg(&p.adj[j - q]) : -1;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] = u[q] >= 0 ? F[u[q]] : 0ull;
+    for (int q = 0; q < 4; ++q) f[q] = u[q] >= 0 ? (Bits)F[u[q]] : 0ull;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint64_t h = f[q] & need;
@@ -105,34 +148,44 @@ __device__ __forceinline__ uint64_t resolve_lane(const BatchParams& p, const uin
   return found;
 }
 
-// The whole warp scans one row from the top, 32 entries per step; returns the
-// bits found (same value in every lane).
-__device__ __forceinline__ uint64_t resolve_warp(const BatchParams& p, const uint64_t* F, int v, long long b,
+// The whole warp scans entries [b, e) of v's row from the top, 128 entries per
+// step (four loads per lane in flight, examined in descending position order);
+// returns the bits found (same value in every lane).  kChunk: the range is one
+// chunk of a longer row, so the first hit of a root is only this chunk's
+// candidate: it is offered with atomicMax and the level is left to the claim.
+template <typename Word, bool kChunk>
+__device__ __forceinline__ uint64_t resolve_warp(const BatchParams& p, const Word* F, int v, long long b,
                                                  long long e, uint64_t need, int lvl, int lane) {
   uint64_t found = 0;
-  for (long long top = e; top > b && need; top -= 32) {
-    const long long j = top - 1 - lane;
-    int u = 0;
-    uint64_t f = 0;
-    if (j >= b) {
-      u = __ldg(&p.adj[j]);
-      f = F[u] & need;
+  for (long long top = e; top > b && need; top -= 128) {
+    int u[4];
+    uint64_t f[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long j = top - 1 - lane - 32 * q;
+      u[q] = j >= b ? __ldg(&p.adj[j]) : 0;
     }
-    const unsigned lo = __reduce_or_sync(kFull, (unsigned)f);
-    const unsigned hi = __reduce_or_sync(kFull, (unsigned)(f >> 32));
-    uint64_t nb = ((uint64_t)hi << 32) | lo;
-    found |= nb;
-    need &= ~nb;
-    while (nb) {  // each new root takes the lowest lane holding its bit (the highest position)
-      const int r = __ffsll((long long)nb) - 1;
-      nb &= nb - 1;
-      const unsigned who = __ballot_sync(kFull, (f >> r) & 1ull);
-      const int src = __ffs(who) - 1;
-      const int pu = __shfl_sync(kFull, u, src);
-      if (lane == 0) {
-        const long long o = (long long)r * p.n + v;
-        p.level[o] = lvl;
-        p.parent[o] = pu;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[q] = (top - 1 - lane - 32 * q >= b) ? ((Bits)F[u[q]] & need) : 0ull;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint64_t nb = warp_or<Word>(f[q]) & need;
+      found |= nb;
+      need &= ~nb;
+      while (nb) {  // each new root takes the lowest lane holding its bit (the highest position)
+        const int r = __ffsll((long long)nb) - 1;
+        nb &= nb - 1;
+        const unsigned who = __ballot_sync(kFull, (f[q] >> r) & 1ull);
+        const int pu = __shfl_sync(kFull, u[q], __ffs(who) - 1);
+        if (lane == 0) {
+          const long long o = (long long)v * p.stride + r;
+          if (kChunk) {
+            atomicMax(&p.sp[o], pu);
+          } else {
+            p.sl[o] = lvl;
+            p.sp[o] = pu;
+          }
+        }
       }
     }
   }
@@ -141,7 +194,8 @@ __device__ __forceinline__ uint64_t resolve_warp(const BatchParams& p, const uin
 
 // Resolves the parents of 32 vertices (one per lane, need = roots to find)
 // against frontier F; lanes with short rows scan alone, long rows get the warp.
-__device__ __forceinline__ uint64_t resolve_group(const BatchParams& p, const uint64_t* F, int v, long long b,
+template <typename Word>
+__device__ __forceinline__ uint64_t resolve_group(const BatchParams& p, const Word* F, int v, long long b,
                                                   long long e, uint64_t need, int lvl, int lane) {
   uint64_t found = 0;
   const bool longrow = need && (e - b) > kShortRow;
@@ -153,28 +207,29 @@ __device__ __forceinline__ uint64_t resolve_group(const BatchParams& p, const ui
     const int lv = __shfl_sync(kFull, v, l);
     const long long lb = __shfl_sync(kFull, b, l), le = __shfl_sync(kFull, e, l);
     const uint64_t ln = __shfl_sync(kFull, need, l);
-    const uint64_t fw = resolve_warp(p, F, lv, lb, le, ln, lvl, lane);
+    const uint64_t fw = resolve_warp<Word, false>(p, F, lv, lb, le, ln, lvl, lane);
     if (lane == l) found = fw;
   }
   return found;
 }
 
 // Top-down visit of edge (u -> w) with frontier bits f of u at level knext - 1.
-__device__ __forceinline__ void td_visit(const BatchParams& p, const uint64_t* Fc, uint64_t* Fn, int knext,
+template <typename Word>
+__device__ __forceinline__ void td_visit(const BatchParams& p, const Word* Fc, Word* Fn, const Word* V, int knext,
                                          uint64_t f, int u, int w, Claims& cl) {
-  const uint64_t nb = f & ~(p.V[w] | Fc[w]);
+  const uint64_t nb = f & ~((Bits)V[w] | (Bits)Fc[w]);
   if (!nb) return;
   for (uint64_t b = nb; b;) {  // u is a parent candidate of w for every new root bit
     const int r = __ffsll((long long)b) - 1;
     b &= b - 1;
-    atomicMax(&p.parent[(long long)r * p.n + w], u);
+    atomicMax(&p.sp[(long long)w * p.stride + r], u);
   }
-  if ((Fn[w] & nb) == nb) return;
-  const unsigned long long old = atomicOr((unsigned long long*)&Fn[w], (unsigned long long)nb);
+  if (((Bits)Fn[w] & nb) == nb) return;
+  const Bits old = atomic_or_word(&Fn[w], nb);
   for (uint64_t b = nb & ~old; b;) {
     const int r = __ffsll((long long)b) - 1;
     b &= b - 1;
-    p.level[(long long)r * p.n + w] = knext;
+    p.sl[(long long)w * p.stride + r] = knext;
   }
   if (old == 0) {
     cta_enqueue(p, knext, cl, w);
@@ -183,42 +238,22 @@ __device__ __forceinline__ void td_visit(const BatchParams& p, const uint64_t* F
   }
 }
 
-// Pull over one kChunkEdges-entry chunk of a long row of v by a whole CTA:
-// each warp takes 64 consecutive entries (two steps of 32, from the top),
-// finds for every root bit of `need` its highest hit, and combines with the
-// other warps and chunks through atomicMax (parents) and atomicOr (F_{k+1}).
-__device__ __forceinline__ void pull_big_chunk(const BatchParams& p, const uint64_t* Fc, uint64_t* Fn, int knext,
-                                               int v, long long rb, long long re, uint64_t need, int lane, int wid,
-                                               Claims& cl, int* wq, int& nbuf) {
-  uint64_t found = 0;
-#pragma unroll
-  for (int step = 0; step < 2; ++step) {
-    const long long j = re - 1 - (long long)wid * 64 - step * 32 - lane;
-    int u = 0;
-    uint64_t f = 0;
-    if (j >= rb) {
-      u = __ldg(&p.adj[j]);
-      f = Fc[u] & need;
-    }
-    const unsigned lo = __reduce_or_sync(kFull, (unsigned)f);
-    const unsigned hi = __reduce_or_sync(kFull, (unsigned)(f >> 32));
-    uint64_t nb = (((uint64_t)hi << 32) | lo) & ~found;
-    found |= nb;
-    while (nb) {
-      const int r = __ffsll((long long)nb) - 1;
-      nb &= nb - 1;
-      const int src = __ffs(__ballot_sync(kFull, (f >> r) & 1ull)) - 1;
-      const int pu = __shfl_sync(kFull, u, src);
-      if (lane == 0) atomicMax(&p.parent[(long long)r * p.n + v], pu);
-    }
-  }
+// Pull over one kChunkEdges-entry chunk [rb, re) of a long row of v by one warp;
+// chunks of the same row combine through atomicMax on the parents and atomicOr
+// on F_{k+1}, whose first setter of a root bit writes that root's level, and
+// whose first setter of any bit claims v for the queue.
+template <typename Word>
+__device__ __forceinline__ void pull_chunk(const BatchParams& p, const Word* Fc, Word* Fn, int knext, int v,
+                                           long long rb, long long re, uint64_t need, int lane, Claims& cl,
+                                           int* wq, int& nbuf) {
+  const uint64_t found = resolve_warp<Word, true>(p, Fc, v, rb, re, need, knext, lane);
   bool claimed = false;
   if (lane == 0 && found) {
-    const unsigned long long old = atomicOr((unsigned long long*)&Fn[v], (unsigned long long)found);
-    for (uint64_t b = found & ~old; b;) {
-      const int r = __ffsll((long long)b) - 1;
-      b &= b - 1;
-      p.level[(long long)r * p.n + v] = knext;
+    const Bits old = atomic_or_word(&Fn[v], found);
+    for (uint64_t bb = found & ~old; bb;) {
+      const int r = __ffsll((long long)bb) - 1;
+      bb &= bb - 1;
+      p.sl[(long long)v * p.stride + r] = knext;
     }
     if (old == 0) {
       claimed = true;
@@ -228,7 +263,10 @@ __device__ __forceinline__ void pull_big_chunk(const BatchParams& p, const uint6
   warp_enqueue(p, knext, wq, nbuf, claimed, v, lane, false);
 }
 
+template <typename Word>
 __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
+  Word* F[3] = {static_cast<Word*>(p.F[0]), static_cast<Word*>(p.F[1]), static_cast<Word*>(p.F[2])};
+  Word* V = static_cast<Word*>(p.V);
   __shared__ Claims cl;
   const int tid = threadIdx.x, lane = tid & 31;
   unsigned epoch = 0;
@@ -243,17 +281,16 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
   const long long gwarp = blockIdx.x + (long long)(tid >> 5) * G;  // round-robin over CTAs
   const unsigned nblocks = gridDim.x;
 
-  // init: outputs to -1, bitsets to 0, counters to 0
-  const long long total = (long long)p.k * p.n;
-  for (long long i = gtid; i < total; i += gthreads) {
-    p.level[i] = -1;
-    p.parent[i] = -1;
-  }
+  // init: scratch parents to -1 (atomicMax offers need a floor; scratch levels
+  // are only read where V says the root reached the vertex), bitsets to 0,
+  // counters to 0
+  const long long total = (long long)p.n * p.stride;
+  for (long long i = gtid; i < total; i += gthreads) p.sp[i] = -1;
   for (long long v = gtid; v < p.n; v += gthreads) {
-    p.F[0][v] = 0;
-    p.F[1][v] = 0;
-    p.F[2][v] = 0;
-    p.V[v] = 0;
+    F[0][v] = 0;
+    F[1][v] = 0;
+    F[2][v] = 0;
+    V[v] = 0;
   }
   if (blockIdx.x == 0 && tid < kCtrRing * (int)(sizeof(LevelCtr) / 8))
     reinterpret_cast<unsigned long long*>(p.ctr)[tid] = 0ull;
@@ -263,11 +300,11 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
   if (blockIdx.x == 0 && tid < p.k) {
     const int s = p.src[tid];
     const uint64_t bit = 1ull << tid;
-    const long long o = (long long)tid * p.n + s;
-    p.level[o] = 0;
-    p.parent[o] = s;
-    atomicOr((unsigned long long*)&p.V[s], (unsigned long long)bit);
-    const unsigned long long old = atomicOr((unsigned long long*)&p.F[0][s], (unsigned long long)bit);
+    const long long o = (long long)s * p.stride + tid;
+    p.sl[o] = 0;
+    p.sp[o] = s;
+    atomic_or_word(&V[s], bit);
+    const Bits old = atomic_or_word(&F[0][s], bit);
     if (old == 0) {
       const unsigned pos = atomicAdd(&p.ctr[0].count, 1u);
       p.queue[0][pos] = s;
@@ -284,14 +321,14 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
     const unsigned count = __ldcg(&p.ctr[k % kCtrRing].count);
     if (count == 0) break;
     const unsigned nchunks = __ldcg(&p.ctr[k % kCtrRing].chunks);
-    const uint64_t* Fc = p.F[k % 3];
-    uint64_t* Fn = p.F[(k + 1) % 3];
+    const Word* Fc = F[k % 3];
+    Word* Fn = F[(k + 1) % 3];
     const int32_t* Q = p.queue[k % 3];
     const int knext = k + 1;
     if (blockIdx.x == 0 && tid < (int)(sizeof(LevelCtr) / 8))
       reinterpret_cast<unsigned long long*>(&p.ctr[(k + 4) % kCtrRing])[tid] = 0ull;
     if (k >= 1) {  // clear F_{k-1} for reuse as F_{k+2}
-      uint64_t* clr = p.F[(k + 2) % 3];
+      Word* clr = F[(k + 2) % 3];
       const unsigned pc = __ldcg(&p.ctr[(k + kCtrRing - 1) % kCtrRing].count);
       if ((long long)pc * 8 < p.n) {
         const int32_t* PQ = p.queue[(k + 2) % 3];
@@ -311,30 +348,30 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         const int u = (int)(it >> 32);
         const long long rb = __ldg(&p.off[u]) + (it & 0xffffffffll) * kChunkEdges;
         const long long re = min(rb + (long long)kChunkEdges, (long long)__ldg(&p.off[u + 1]));
-        const uint64_t f = Fc[u];
-        for (long long j = rb + tid; j < re; j += kBBlock) td_visit(p, Fc, Fn, knext, f, u, __ldg(&p.adj[j]), cl);
+        const uint64_t f = (Bits)Fc[u];
+        for (long long j = rb + tid; j < re; j += kBBlock) td_visit(p, Fc, Fn, V, knext, f, u, __ldg(&p.adj[j]), cl);
       }
       // other frontier rows: one warp each; every frontier vertex folds its bits into V
       for (long long i = gwarp; i < count; i += gwarps) {
         const int u = Q[i];
-        const uint64_t f = Fc[u];
-        if (lane == 0) p.V[u] |= f;
+        const uint64_t f = (Bits)Fc[u];
+        if (lane == 0) V[u] = (Word)((Bits)V[u] | f);
         const long long b = __ldg(&p.off[u]), e = __ldg(&p.off[u + 1]);
         if (e - b > kChunkEdges) continue;
-        for (long long j = b + lane; j < e; j += 32) td_visit(p, Fc, Fn, knext, f, u, __ldg(&p.adj[j]), cl);
+        for (long long j = b + lane; j < e; j += 32) td_visit(p, Fc, Fn, V, knext, f, u, __ldg(&p.adj[j]), cl);
       }
     } else {
       int* wq = cl.wq[wid];
       int nbuf = 0;
-      // long rows: one CTA per chunk of the static table
-      for (long long ci = blockIdx.x; ci < p.nbig; ci += G) {
+      // long rows: one warp per chunk of the static table
+      for (long long ci = gwarp; ci < p.nbig; ci += gwarps) {
         const int64_t it = p.big[ci];
         const int v = (int)(it >> 32);
-        const uint64_t need = ~(p.V[v] | Fc[v]) & p.mask;
+        const uint64_t need = __shfl_sync(kFull, ~((Bits)V[v] | (Bits)Fc[v]) & p.mask, 0);
         if (!need) continue;
         const long long rb = __ldg(&p.off[v]) + (it & 0xffffffffll) * kChunkEdges;
         const long long re = min(rb + (long long)kChunkEdges, (long long)__ldg(&p.off[v + 1]));
-        pull_big_chunk(p, Fc, Fn, knext, v, rb, re, need, lane, wid, cl, wq, nbuf);
+        pull_chunk(p, Fc, Fn, knext, v, rb, re, need, lane, cl, wq, nbuf);
       }
       // other rows: 32 vertices per warp; the owner lane updates V and F_{k+1}
       const long long nw = ((long long)p.n + 31) / 32;
@@ -344,8 +381,8 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         uint64_t need = 0, vv = 0, fv = 0;
         long long b = 0, e = 0;
         if (v0 < p.n) {
-          vv = p.V[v];
-          fv = Fc[v];
+          vv = (Bits)V[v];
+          fv = (Bits)Fc[v];
           need = ~(vv | fv) & p.mask;
           if (need) {
             b = __ldg(&p.off[v]);
@@ -356,8 +393,8 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         const uint64_t found = resolve_group(p, Fc, v, b, e, need, knext, lane);
         if (v0 < p.n) {
           const uint64_t nv = vv | fv | found;
-          if (nv != vv) p.V[v] = nv;
-          if (found) Fn[v] = found;
+          if (nv != vv) V[v] = (Word)nv;
+          if (found) Fn[v] = (Word)found;
         }
         warp_enqueue(p, knext, wq, nbuf, found != 0, v, lane, false);
       }
@@ -376,6 +413,37 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
     }
   }
   if (gtid == 0) p.misc[1] = k;
+
+  // transpose the scratch rows of 32 vertices into the root-major outputs
+  // (the loop ended right after a grid barrier, so the scratch is final, and V
+  // holds every root bit of every vertex reached)
+  int* tl = cl.cq;                  // [stride][33] levels
+  int* tp = cl.cq + 64 * 33;        // [stride][33] parents
+  const int S = p.stride;
+  const long long ntiles = ((long long)p.n + 31) / 32;
+  for (long long t = blockIdx.x; t < ntiles; t += G) {
+    const long long v0 = t * 32;
+    const int nv = (int)min(32ll, (long long)p.n - v0);
+    for (int e = tid; e < 32 * S; e += kBBlock) {
+      const int i = e / S, r = e - i * S;
+      if (i < nv) {
+        const long long o = (v0 + i) * S + r;
+        const bool reached = ((Bits)V[v0 + i] >> r) & 1ull;
+        tl[r * 33 + i] = reached ? p.sl[o] : -1;
+        tp[r * 33 + i] = p.sp[o];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < 32 * p.k; e += kBBlock) {
+      const int r = e >> 5, i = e & 31;
+      if (i < nv) {
+        const long long o = (long long)r * p.n + v0 + i;
+        p.level[o] = tl[r * 33 + i];
+        p.parent[o] = tp[r * 33 + i];
+      }
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -385,7 +453,9 @@ int launch_batch(const BatchRequest& r, cudaStream_t s) {
   Workspace* w = r.w;
   DeviceInfo di;
   if (int e = current_device_info(&di)) return e;
-  if (r.k < 1 || r.k > 64) return fail(BFS_ERR_INVALID_ARG, "batch of 1..64 roots expected");
+  if (r.width != 8 && r.width != 16 && r.width != 32 && r.width != 64)
+    return fail(BFS_ERR_INVALID_ARG, "batch width must be 8, 16, 32 or 64");
+  if (r.k < 1 || r.k > r.width) return fail(BFS_ERR_INVALID_ARG, "batch of 1..width roots expected");
   if (int e = ensure_batch_state(g, w)) return e;
   const bfs_tuning t = effective_tuning(g);
   BatchParams p{};
@@ -398,6 +468,9 @@ int launch_batch(const BatchRequest& r, cudaStream_t s) {
   for (int i = 0; i < r.k; ++i) p.src[i] = r.h_sources[i];
   p.level = r.level;
   p.parent = r.parent;
+  p.stride = r.width;
+  p.sl = w->bscr;
+  p.sp = w->bscr + (size_t)g->n * 64;
   for (int i = 0; i < 3; ++i) {
     p.F[i] = w->bset[i];
     p.queue[i] = w->queue[i];
@@ -414,12 +487,15 @@ int launch_batch(const BatchRequest& r, cudaStream_t s) {
   p.stats = r.want_stats ? w->stats : nullptr;
   p.spin_limit = r.spin_limit ? r.spin_limit : (1u << 25);
   p.td_limit = t.batch_topdown_limit;
+  const void* fn = r.width == 8    ? (const void*)batch_kernel<uint8_t>
+                   : r.width == 16 ? (const void*)batch_kernel<uint16_t>
+                   : r.width == 32 ? (const void*)batch_kernel<uint32_t>
+                                   : (const void*)batch_kernel<uint64_t>;
   int per_sm = 0;
-  BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBBlock, 0));
+  BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBBlock, 0));
   if (per_sm < 1) return fail(BFS_ERR_CUDA, "batch kernel cannot be resident");
   void* args[] = {&p};
-  BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(per_sm * di.sm_count), dim3(kBBlock),
-                                           args, 0, s));
+  BFS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(per_sm * di.sm_count), dim3(kBBlock), args, 0, s));
   return BFS_OK;
 }
 

@@ -25,6 +25,7 @@ constexpr int kClaimWarps = kClaimBlock / 32;
 constexpr int kQBuf = 6144;               // per-CTA buffer of next-frontier vertices (top-down claims)
 constexpr int kWQBuf = 256;               // per-warp buffer of next-frontier vertices (pull claims)
 constexpr int kBigBuf = 2 * kClaimBlock;  // per-CTA buffer of claimed vertices above the chunk degree
+static_assert(kQBuf >= 2 * 64 * 33, "the batched transpose tiles live in the CTA buffer");
 
 struct Claims {
   int qn;    // entries in cq (may exceed kQBuf: the excess went straight to the queue)

@@ -76,6 +76,7 @@ struct Workspace {
   // batched (64-root bitset) state, lazily
   uint64_t* bset[3] = {nullptr, nullptr, nullptr};
   uint64_t* bvis = nullptr;
+  int32_t* bscr = nullptr;  // batched: vertex-major scratch results, levels then parents, int32[2][n][64]
   // pinned host staging for schedules and multi-source seeds; `stage_ev` is
   // recorded after each copy out of it and waited on before it is rewritten
   int32_t* h_stage = nullptr;
@@ -157,7 +158,8 @@ struct BatchRequest {
   bfs_graph* g = nullptr;
   Workspace* w = nullptr;
   const int32_t* h_sources = nullptr;  // up to 64
-  int32_t k = 0;
+  int32_t k = 0;              // roots, at most width
+  int32_t width = 64;         // bits per frontier word: 8, 16, 32 or 64
   int32_t* level = nullptr;   // device [k][n]
   int32_t* parent = nullptr;
   unsigned spin_limit = 0;

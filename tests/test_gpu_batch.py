@@ -1,4 +1,4 @@
-"""GPU parity of the batched (64-root bitset) and ragged (union of graphs) traversals:
+"""GPU parity of the batched (8- to 64-root bitset) and ragged (union of graphs) traversals:
 every output row equals the oracle's BFS from that root, bit for bit."""
 import numpy as np
 import pytest
@@ -17,11 +17,14 @@ def _cuda():
     require_cuda()
 
 
-def check_batch(el, roots, td_limit=None):
+def check_batch(el, roots, td_limit=None, width=None):
     og = oracle.csr_of(el)
     g = device_graph_from_edges(el)
     if td_limit is not None:
         bfs.bfs_set_tuning(g, batch_topdown_limit=td_limit)
+    if width is not None:
+        bfs.bfs_set_tuning(g, batch_width=width)
+        assert bfs.bfs_get_tuning(g).batch_width == width
     parent, level = bfs.run_batch(g, list(roots))
     bfs.bfs_sync(g)
     parent, level = parent.cpu().numpy(), level.cpu().numpy()
@@ -31,24 +34,35 @@ def check_batch(el, roots, td_limit=None):
     return g
 
 
+@pytest.mark.parametrize("width", [8, 16, 32, 64])
 @pytest.mark.parametrize("td_limit", [None, 1, 1 << 30])
-def test_batch_s16_64_roots(td_limit):
+def test_batch_s16_64_roots(td_limit, width):
     el, roots = inputs.workload_rmat(16, 64, graph_seed=1, root_seed=101)
-    check_batch(el, roots, td_limit)
+    check_batch(el, roots, td_limit, width)
 
 
-def test_batch_ragged_sizes_and_repeats():
+@pytest.mark.parametrize("width", [8, 64])
+def test_batch_ragged_sizes_and_repeats(width):
     el = inputs.rmat(13, 16, seed=8)
     r = inputs.roots(el, 70, 9)
-    roots = list(r[:65]) + [int(r[0]), int(r[0])] + [0]  # 68 roots: two chunks, repeated roots, a maybe-isolated one
-    check_batch(el, roots)
-    check_batch(el, roots[:1])
+    roots = list(r[:65]) + [int(r[0]), int(r[0])] + [0]  # 68 roots: several chunks, repeated roots, a maybe-isolated one
+    check_batch(el, roots, width=width)
+    check_batch(el, roots[:1], width=width)
 
 
-def test_batch_closed_forms():
-    check_batch(inputs.grid3d(12), [0, 5, 1727, 100])
-    check_batch(inputs.star(70000), [0, 1, 2])
-    check_batch(inputs.path(3000), list(range(0, 3000, 97)))
+@pytest.mark.parametrize("width", [8, 16, 64])
+def test_batch_closed_forms(width):
+    check_batch(inputs.grid3d(12), [0, 5, 1727, 100], width=width)
+    check_batch(inputs.star(70000), [0, 1, 2], width=width)
+    check_batch(inputs.path(3000), list(range(0, 3000, 97)), width=width)
+
+
+def test_batch_width_default_and_rejects():
+    g = device_graph_from_edges(inputs.path(100))
+    assert bfs.bfs_get_tuning(g).batch_width == 64
+    bfs.bfs_set_tuning(g, batch_width=12)  # not a word width: the default applies
+    assert bfs.bfs_get_tuning(g).batch_width == 64
+    g.destroy()
 
 
 def test_batch_s22_64_roots():

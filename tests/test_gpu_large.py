@@ -52,11 +52,16 @@ def test_rmat26_single_root_bench_configuration():
 
 
 def test_rmat24_batched_64_roots():
-    """Batched traversal of 64 roots on R-MAT scale 24 (graph seed 4 / roots 104): every row validated."""
+    """64 roots in one batched traversal with 64-bit words on R-MAT scale 24 (graph seed 4 /
+    roots 104): every row validated; four traversals of 16-bit words give the same rows."""
     el, roots = inputs.workload_rmat(24, 64, graph_seed=4, root_seed=104)
     g = device_graph_from_edges(el)
     parent, level = bfs.run_batch(g, [int(s) for s in roots])
+    bfs.bfs_set_tuning(g, batch_width=16)
+    p2, l2 = bfs.run_batch(g, [int(s) for s in roots])
     bfs.bfs_sync(g)
+    assert torch.equal(parent, p2) and torch.equal(level, l2)
+    del p2, l2
     lv, pa = level.cpu().numpy(), parent.cpu().numpy()
     del parent, level
     g.destroy()
