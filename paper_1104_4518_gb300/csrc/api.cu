@@ -744,7 +744,7 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
         }
         float ms = 0.0f;
         rc = time_plain(t, &ms);
-        if (!rc && ms < cur_ms) {
+        if (!rc && ms < 0.97f * cur_ms) {  // a change must beat the timing noise of a few roots
           cur_ms = ms;
           cur = t;
         }
@@ -760,7 +760,7 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
       t.batch_topdown_limit = std::max(1, (int)(g->n * fr[c]));
       float ms = 0.0f;
       rc = time_batch(t, &ms);
-      if (!rc && ms < bms) {
+      if (!rc && ms < 0.97f * bms) {
         bms = ms;
         cur = t;
       }
@@ -770,7 +770,7 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
       t.batch_width = wbits;
       float ms = 0.0f;
       rc = time_batch(t, &ms);
-      if (!rc && ms < bms) {
+      if (!rc && ms < 0.97f * bms) {
         bms = ms;
         cur = t;
       }

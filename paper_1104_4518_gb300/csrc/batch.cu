@@ -416,30 +416,50 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
 
   // transpose the scratch rows of 32 vertices into the root-major outputs
   // (the loop ended right after a grid barrier, so the scratch is final, and V
-  // holds every root bit of every vertex reached)
-  int* tl = cl.cq;                  // [stride][33] levels
-  int* tp = cl.cq + 64 * 33;        // [stride][33] parents
-  const int S = p.stride;
+  // holds every root bit of every vertex reached).  Scratch rows are read as
+  // int4 (S is a multiple of 4 and the scratch 16-byte aligned); output rows
+  // are written as int4 when n is a multiple of 4 and both outputs start on a
+  // 16-byte boundary (every row then does), else one int at a time.
+  int* tl = cl.cq;            // [S][33] levels
+  int* tp = cl.cq + 64 * 33;  // [S][33] parents
+  const int S = p.stride, S4 = S / 4;
+  const bool vec_out = (p.n & 3) == 0 &&
+                       ((reinterpret_cast<uintptr_t>(p.level) | reinterpret_cast<uintptr_t>(p.parent)) & 15u) == 0;
   const long long ntiles = ((long long)p.n + 31) / 32;
   for (long long t = blockIdx.x; t < ntiles; t += G) {
     const long long v0 = t * 32;
     const int nv = (int)min(32ll, (long long)p.n - v0);
-    for (int e = tid; e < 32 * S; e += kBBlock) {
-      const int i = e / S, r = e - i * S;
+    for (int e = tid; e < 32 * S4; e += kBBlock) {
+      const int i = e / S4, c = e - i * S4;
       if (i < nv) {
-        const long long o = (v0 + i) * S + r;
-        const bool reached = ((Bits)V[v0 + i] >> r) & 1ull;
-        tl[r * 33 + i] = reached ? p.sl[o] : -1;
-        tp[r * 33 + i] = p.sp[o];
+        const long long o = (v0 + i) * S + 4 * c;
+        const int4 lv = *reinterpret_cast<const int4*>(p.sl + o);
+        const int4 pv = *reinterpret_cast<const int4*>(p.sp + o);
+        const Bits vv = (Bits)V[v0 + i] >> (4 * c);
+        tl[(4 * c + 0) * 33 + i] = (vv & 1ull) ? lv.x : -1;
+        tl[(4 * c + 1) * 33 + i] = (vv & 2ull) ? lv.y : -1;
+        tl[(4 * c + 2) * 33 + i] = (vv & 4ull) ? lv.z : -1;
+        tl[(4 * c + 3) * 33 + i] = (vv & 8ull) ? lv.w : -1;
+        tp[(4 * c + 0) * 33 + i] = pv.x;
+        tp[(4 * c + 1) * 33 + i] = pv.y;
+        tp[(4 * c + 2) * 33 + i] = pv.z;
+        tp[(4 * c + 3) * 33 + i] = pv.w;
       }
     }
     __syncthreads();
-    for (int e = tid; e < 32 * p.k; e += kBBlock) {
-      const int r = e >> 5, i = e & 31;
-      if (i < nv) {
-        const long long o = (long long)r * p.n + v0 + i;
-        p.level[o] = tl[r * 33 + i];
-        p.parent[o] = tp[r * 33 + i];
+    for (int e = tid; e < 8 * p.k; e += kBBlock) {
+      const int r = e >> 3, i = 4 * (e & 7);
+      const long long o = (long long)r * p.n + v0 + i;
+      const int* L = tl + r * 33 + i;
+      const int* P = tp + r * 33 + i;
+      if (vec_out && i + 4 <= nv) {
+        *reinterpret_cast<int4*>(p.level + o) = make_int4(L[0], L[1], L[2], L[3]);
+        *reinterpret_cast<int4*>(p.parent + o) = make_int4(P[0], P[1], P[2], P[3]);
+      } else {
+        for (int m = 0; m < 4 && i + m < nv; ++m) {
+          p.level[o + m] = L[m];
+          p.parent[o + m] = P[m];
+        }
       }
     }
     __syncthreads();

@@ -118,3 +118,26 @@ def test_ragged_rejects_source_outside_part():
     with pytest.raises(bfs.BfsError) as e:
         bfs.bfs_run_ragged(u, [0, 5], outs, outs)
     assert e.value.code == bfs.BFS_ERR_INVALID_ARG
+
+
+def test_batch_unaligned_outputs_and_odd_n():
+    """The output transpose takes its scalar path for n not a multiple of 4 and for output
+    rows that do not start on a 16-byte boundary; results are the same."""
+    for n_extra in (0, 1, 2, 3):
+        el = inputs.rmat(11, 16, seed=30 + n_extra)
+        if n_extra:
+            el, _ = inputs.disjoint_union([el, inputs.path(n_extra + 1)])
+        og = oracle.csr_of(el)
+        g = device_graph_from_edges(el)
+        roots = [int(r) for r in inputs.roots(el, 9, 4)]
+        n = el.n
+        buf = torch.empty(2 * (len(roots) * n + 1), dtype=torch.int32, device="cuda")
+        level = buf[1:1 + len(roots) * n]  # 4-byte aligned, not 16-byte aligned
+        parent = buf[2 + len(roots) * n:2 + 2 * len(roots) * n]
+        bfs.bfs_run_batch(g, roots, parent, level)
+        bfs.bfs_sync(g)
+        lv = level.view(len(roots), n).cpu().numpy()
+        pa = parent.view(len(roots), n).cpu().numpy()
+        for i, s in enumerate(roots):
+            assert_same(oracle.bfs(og, s), (lv[i], pa[i]), f"n={n} root {s}")
+        g.destroy()
