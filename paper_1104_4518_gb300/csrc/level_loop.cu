@@ -518,29 +518,61 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   const long long gthreads = (long long)gridDim.x * kBlock;
   const unsigned nblocks = gridDim.x;
 
-  // ---- init: outputs to -1, bitmaps cleared, counters zeroed.  One warp per
-  // bitmap word.  Vertices without edges (and the tail beyond n) start as
-  // visited, since no traversal can reach them.  A single source is seeded in
-  // the same phase; several sources (ragged runs) get a seeding phase of their own.
+  // ---- init: outputs to -1, bitmaps cleared, counters zeroed.  Vertices
+  // without edges (and the tail beyond n) start as visited, since no traversal
+  // can reach them.  A single source is seeded in the same phase; several
+  // sources (ragged runs) get a seeding phase of their own.  The output fill
+  // only stores and the bitmap loop's loads are independent, so neither waits
+  // on a load per step.
   const bool single = p.nsources == 1;
   const int s0 = p.src0;
-  const long long nv32 = (long long)p.nwords * 32;
-  for (long long v = gtid; v < nv32; v += gthreads) {
-    bool dead = true;
-    if (v < p.n) {
-      const bool src = single && v == s0;
-      p.level[v] = src ? 0 : -1;
-      p.parent[v] = src ? s0 : -1;
-      dead = src || (p.dead == nullptr && __ldg(&p.off[v + 1]) == __ldg(&p.off[v]));
+  // outputs: 4 vertices per thread and step, one 16-byte store each when aligned
+  const bool vec = ((reinterpret_cast<uintptr_t>(p.level) | reinterpret_cast<uintptr_t>(p.parent)) & 15u) == 0;
+  const long long n4 = ((long long)p.n + 3) / 4;
+  for (long long q = gtid; q < n4; q += gthreads) {
+    const long long v = 4 * q;
+    int lv[4], pv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const bool src = single && v + c == s0;
+      lv[c] = src ? 0 : -1;
+      pv[c] = src ? s0 : -1;
     }
-    unsigned dm = __ballot_sync(kFull, dead);
-    if ((tid & 31) == 0) {
-      const long long w = v >> 5;
-      if (p.dead != nullptr) dm |= __ldg(&p.dead[w]);
-      p.bits[0][w] = (single && w == (s0 >> 5)) ? (1u << (s0 & 31)) : 0u;
+    if (vec && v + 4 <= p.n) {
+      *reinterpret_cast<int4*>(p.level + v) = make_int4(lv[0], lv[1], lv[2], lv[3]);
+      *reinterpret_cast<int4*>(p.parent + v) = make_int4(pv[0], pv[1], pv[2], pv[3]);
+    } else {
+      for (int c = 0; c < 4 && v + c < p.n; ++c) {
+        p.level[v + c] = lv[c];
+        p.parent[v + c] = pv[c];
+      }
+    }
+  }
+  // bitmaps: vis starts as the edgeless vertices (and the tail beyond n) plus
+  // the single source; one thread per word when the dead bits are precomputed
+  const uint32_t srcbit = 1u << (s0 & 31);
+  const long long sw = s0 >> 5;
+  if (p.dead != nullptr) {
+    for (long long w = gtid; w < p.nwords; w += gthreads) {
+      const bool sword = single && w == sw;
+      p.vis[w] = __ldg(&p.dead[w]) | (sword ? srcbit : 0u);
+      p.bits[0][w] = sword ? srcbit : 0u;
       p.bits[1][w] = 0;
       p.bits[2][w] = 0;
-      p.vis[w] = dm;
+    }
+  } else {  // dead bits from the row offsets, one warp per word
+    const long long nv32 = (long long)p.nwords * 32;
+    for (long long v = gtid; v < nv32; v += gthreads) {
+      const bool dead = v >= p.n || (single && v == s0) || __ldg(&p.off[v + 1]) == __ldg(&p.off[v]);
+      const unsigned dm = __ballot_sync(kFull, dead);
+      if ((tid & 31) == 0) {
+        const long long w = v >> 5;
+        const bool sword = single && w == sw;
+        p.vis[w] = dm;
+        p.bits[0][w] = sword ? srcbit : 0u;
+        p.bits[1][w] = 0;
+        p.bits[2][w] = 0;
+      }
     }
   }
   if (blockIdx.x == 0) {
