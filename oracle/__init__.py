@@ -60,6 +60,12 @@ def _load():
             lib.oracle_component_edges.argtypes = [i64p, i32p, ctypes.c_int32]
             lib.oracle_level_stats.restype = ctypes.c_int
             lib.oracle_level_stats.argtypes = [i64p, i32p, ctypes.c_int32, ctypes.c_int32, i64p, i64p]
+            lib.oracle_build_digraph_csr.restype = ctypes.c_int64
+            lib.oracle_build_digraph_csr.argtypes = [i32p, i32p, ctypes.c_int64, ctypes.c_int32, i64p, i32p]
+            lib.oracle_bfs_directed.restype = ctypes.c_int32
+            lib.oracle_bfs_directed.argtypes = [i64p, i32p, ctypes.c_int32, ctypes.c_int32, i32p, i32p, i32p]
+            lib.oracle_out_edges.restype = ctypes.c_int64
+            lib.oracle_out_edges.argtypes = [i64p, i32p, ctypes.c_int32]
             lib.oracle_validate_edges.restype = ctypes.c_int64
             lib.oracle_validate_edges.argtypes = [i32p, i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i32p,
                                                   i32p, i32p, i64p]
@@ -125,6 +131,46 @@ def bfs(g: CSR, s: int):
     if nl < 0:
         raise ValueError("oracle_bfs: bad source")
     return level, parent, int(nl)
+
+
+def digraph_csr(src: np.ndarray, dst: np.ndarray, n: int) -> CSR:
+    """Directed CSR: row u holds the heads of the arcs u -> v, sorted, repeats and
+    self-loops dropped (the non-symmetric A of Sec. 3.2)."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = int(src.shape[0])
+    offsets = np.empty(n + 1, dtype=np.int64)
+    adj = np.empty(max(m, 1), dtype=np.int32)
+    nnz = _load().oracle_build_digraph_csr(_p(src, ctypes.c_int32), _p(dst, ctypes.c_int32), m, n,
+                                           _p(offsets, ctypes.c_int64), _p(adj, ctypes.c_int32))
+    if nnz < 0:
+        raise ValueError("oracle_build_digraph_csr: endpoint out of range")
+    return CSR(offsets, adj[:nnz].copy())
+
+
+def digraph_of(g) -> CSR:
+    """Directed CSR of an `inputs.EdgeList` (arcs src -> dst)."""
+    return digraph_csr(g.src, g.dst, g.n)
+
+
+def bfs_directed(g: CSR, s: int):
+    """(level, parent, nlevels) of the BFS from s along the arcs of a directed CSR:
+    level = shortest directed path length, parent = largest in-neighbour one level up."""
+    n = g.n
+    level = np.empty(n, dtype=np.int32)
+    parent = np.empty(n, dtype=np.int32)
+    queue = np.empty(n, dtype=np.int32)
+    nl = _load().oracle_bfs_directed(_p(g.offsets, ctypes.c_int64), _p(g.adj, ctypes.c_int32), n, int(s),
+                                     _p(level, ctypes.c_int32), _p(parent, ctypes.c_int32),
+                                     _p(queue, ctypes.c_int32))
+    if nl < 0:
+        raise ValueError("oracle_bfs_directed: bad source")
+    return level, parent, int(nl)
+
+
+def out_edges(g: CSR, level: np.ndarray) -> int:
+    """TEPS edge count of a directed traversal: arcs leaving reached vertices."""
+    return int(_load().oracle_out_edges(_p(g.offsets, ctypes.c_int64), _p(level, ctypes.c_int32), g.n))
 
 
 def bfs_many(g: CSR, sources, threads: int | None = None):

@@ -20,6 +20,10 @@
  *     output contract).
  *   - TEPS edge count of a traversal: the undirected edges inside the reached
  *     component, half the degree sum of the reached vertices (Sec. 6).
+ *   - directed graphs (the paper's matrix A of Sec. 3.2 need not be symmetric;
+ *     the traversal then multiplies by A^T): rows hold out-neighbours only,
+ *     level[v] is the length of the shortest directed path s -> v, and
+ *     parent[v] the largest id u with an arc u -> v and level[u] = level[v] - 1.
  *
  * Algorithm: the queue-based serial BFS the paper contrasts with its two-stack
  * Algorithm 1 (Sec. 2.1 -- both give the same levels), followed by a separate
@@ -194,4 +198,85 @@ int64_t oracle_validate_edges(const int32_t* src, const int32_t* dst, int64_t m,
     }
   }
   return bad[0] + bad[1] + bad[2] + bad[3];
+}
+
+/*
+ * Directed CSR of an edge list: row u holds the heads v of the arcs u -> v,
+ * sorted, repeats and self-loops dropped.  offsets: int64[n+1], adj: int32
+ * scratch of capacity m.  Returns nnz, or -1 on a bad argument.
+ */
+int64_t oracle_build_digraph_csr(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
+                                 int64_t* offsets, int32_t* adj) {
+  if (n < 0 || m < 0 || !offsets || (m > 0 && (!src || !dst || !adj))) return -1;
+  for (int64_t e = 0; e < m; ++e)
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return -1;
+  int64_t* fill = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!fill) return -1;
+  for (int64_t i = 0; i <= n; ++i) offsets[i] = 0;
+  for (int64_t e = 0; e < m; ++e)
+    if (src[e] != dst[e]) offsets[src[e] + 1] += 1;
+  for (int64_t v = 0; v < n; ++v) offsets[v + 1] += offsets[v];
+  for (int64_t v = 0; v < n; ++v) fill[v] = offsets[v];
+  for (int64_t e = 0; e < m; ++e)
+    if (src[e] != dst[e]) adj[fill[src[e]]++] = dst[e];
+  int64_t out = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t b = offsets[v], e = offsets[v + 1];
+    qsort(adj + b, (size_t)(e - b), sizeof(int32_t), oracle_cmp_i32);
+    int64_t row_start = out;
+    for (int64_t i = b; i < e; ++i) {
+      if (i > b && adj[i] == adj[i - 1]) continue;
+      adj[out++] = adj[i];
+    }
+    offsets[v] = row_start;
+  }
+  offsets[n] = out;
+  free(fill);
+  return out;
+}
+
+/*
+ * Serial BFS from s over the out-rows of a directed CSR; the parent pass runs
+ * over every arc u -> v and keeps, for each v, the largest u one level closer.
+ * Same outputs and return value as oracle_bfs.
+ */
+int32_t oracle_bfs_directed(const int64_t* offsets, const int32_t* adj, int32_t n, int32_t s,
+                            int32_t* level, int32_t* parent, int32_t* queue) {
+  if (n <= 0 || s < 0 || s >= n || !offsets || !level || !parent || !queue) return -1;
+  for (int32_t v = 0; v < n; ++v) {
+    level[v] = -1;
+    parent[v] = -1;
+  }
+  int64_t head = 0, tail = 0;
+  level[s] = 0;
+  queue[tail++] = s;
+  int32_t deepest = 0;
+  while (head < tail) {
+    int32_t u = queue[head++];
+    for (int64_t i = offsets[u]; i < offsets[u + 1]; ++i) {
+      int32_t v = adj[i];
+      if (level[v] == -1) {
+        level[v] = level[u] + 1;
+        if (level[v] > deepest) deepest = level[v];
+        queue[tail++] = v;
+      }
+    }
+  }
+  for (int32_t u = 0; u < n; ++u) {
+    if (level[u] < 0) continue;
+    for (int64_t i = offsets[u]; i < offsets[u + 1]; ++i) {
+      int32_t v = adj[i];
+      if (v != s && level[v] == level[u] + 1 && u > parent[v]) parent[v] = u;
+    }
+  }
+  parent[s] = s;
+  return deepest + 1;
+}
+
+/* Arcs leaving the reached set (the TEPS count of a directed traversal). */
+int64_t oracle_out_edges(const int64_t* offsets, const int32_t* level, int32_t n) {
+  int64_t sum = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (level[v] >= 0) sum += offsets[v + 1] - offsets[v];
+  return sum;
 }
