@@ -58,6 +58,7 @@ typedef enum bfs_status {
 /* Flags of bfs_graph_create / bfs_graph_create_from_edges / bfs_opts.flags. */
 #define BFS_HOST_PTRS 0x1u /* the input (graph create) or output (run) pointers are host memory */
 #define BFS_VALIDATE 0x2u  /* graph create: check the CSR on the device before accepting it */
+#define BFS_DIRECTED 0x4u  /* graph create: the arcs are directed (see below) */
 
 /* Per-level expansion variants (each gives identical levels and parents). */
 typedef enum bfs_variant {
@@ -134,6 +135,18 @@ typedef struct bfs_graph bfs_graph;
  * self-loops, symmetric) and BFS_ERR_INVALID_GRAPH is returned if it fails.
  * Without it a malformed CSR gives unspecified (but memory-safe for in-range
  * ids) results.  Requires 1 <= n < 2^31 - 1 and 0 <= nnz < 2^40.
+ *
+ * With BFS_DIRECTED the CSR holds the arcs of a directed graph: row u lists the
+ * heads v of the arcs u -> v (sorted, no repeats, no self-loops; symmetry is
+ * not required).  Every traversal then follows the arcs: level[v] is the
+ * length of the shortest directed path s -> v and parent[v] the largest id u
+ * with an arc u -> v and level[u] = level[v] - 1 (the product with A^T of
+ * Sec. 3.2 when A is not symmetric).  The library also builds the transpose
+ * on the device (about 8 bytes per arc more), which the pull variant scans;
+ * the TEPS count (bfs_opts.edges_out) is the number of arcs leaving reached
+ * vertices.  Directed graphs cannot be parts of bfs_graph_union
+ * (BFS_ERR_UNSUPPORTED); bfs_graph_csr and bfs_graph_copy_csr give the
+ * out-rows.
  */
 BFS_API int bfs_graph_create(const int64_t* offsets, const int32_t* adj, int32_t n, int64_t nnz,
                      uint32_t flags, bfs_graph** out);
@@ -145,7 +158,9 @@ BFS_API int bfs_graph_create(const int64_t* offsets, const int32_t* adj, int32_t
  * row offsets from the sorted keys (the symmetrised, deduplicated input of the
  * paper's benchmark, Sec. 6).  Endpoints outside [0, n) give
  * BFS_ERR_INVALID_ARG.  Temporary device memory of about 40 bytes per edge is
- * allocated and released inside the call, which synchronises `stream`.
+ * allocated and released inside the call, which synchronises `stream`.  With
+ * BFS_DIRECTED the pairs are arcs src -> dst: nothing is symmetrised, and the
+ * graph is the directed graph of bfs_graph_create with BFS_DIRECTED.
  */
 BFS_API int bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
                                 uint32_t flags, void* stream, bfs_graph** out);

@@ -33,6 +33,7 @@ BFS_ERR_UNSUPPORTED = 6
 
 BFS_HOST_PTRS = 0x1
 BFS_VALIDATE = 0x2
+BFS_DIRECTED = 0x4
 
 BFS_VARIANT_TD_THREAD = 0
 BFS_VARIANT_TD_WARP = 1
@@ -218,28 +219,31 @@ class Graph:
 
 # ---------------- graph construction ----------------
 
-def bfs_graph_create(offsets, adj, validate: bool = False) -> Graph:
-    """Graph from a CSR (int64 offsets[n+1], int32 adj[nnz]) on device or host."""
+def bfs_graph_create(offsets, adj, validate: bool = False, directed: bool = False) -> Graph:
+    """Graph from a CSR (int64 offsets[n+1], int32 adj[nnz]) on device or host; with
+    `directed`, row u lists the heads of the arcs u -> v (BFS_DIRECTED)."""
     po, ho = _ptr_and_host(offsets, "int64")
     pa, ha = _ptr_and_host(adj, "int32")
     if ho != ha:
         raise ValueError("offsets and adj must both be host or both be device memory")
     n = int(offsets.shape[0]) - 1
     nnz = int(adj.shape[0])
-    flags = (BFS_HOST_PTRS if ho else 0) | (BFS_VALIDATE if validate else 0)
+    flags = (BFS_HOST_PTRS if ho else 0) | (BFS_VALIDATE if validate else 0) | (BFS_DIRECTED if directed else 0)
     h = ctypes.c_void_p()
     _check(lib().bfs_graph_create(po, pa, n, nnz, flags, ctypes.byref(h)))
     return Graph(h)
 
 
-def bfs_graph_create_from_edges(src, dst, n: int, stream=None) -> Graph:
-    """Graph from an undirected edge list (int32 src/dst) on device or host."""
+def bfs_graph_create_from_edges(src, dst, n: int, stream=None, directed: bool = False) -> Graph:
+    """Graph from an edge list (int32 src/dst) on device or host: undirected, or the
+    arcs src -> dst with `directed` (BFS_DIRECTED)."""
     ps, hs = _ptr_and_host(src, "int32")
     pd, hd = _ptr_and_host(dst, "int32")
     if hs != hd:
         raise ValueError("src and dst must both be host or both be device memory")
     h = ctypes.c_void_p()
-    _check(lib().bfs_graph_create_from_edges(ps, pd, int(src.shape[0]), int(n), BFS_HOST_PTRS if hs else 0,
+    flags = (BFS_HOST_PTRS if hs else 0) | (BFS_DIRECTED if directed else 0)
+    _check(lib().bfs_graph_create_from_edges(ps, pd, int(src.shape[0]), int(n), flags,
                                              _stream_handle(stream), ctypes.byref(h)))
     return Graph(h)
 

@@ -191,12 +191,18 @@ static int check_graph(const bfs_graph* g) {
   return BFS_OK;
 }
 
-static int make_graph_from_device_csr(int64_t* d_off, int32_t* d_adj, int32_t n, int64_t nnz, bfs_graph** out) {
+// Takes ownership of the out-rows (d_off, d_adj) and, for a directed graph, of
+// the in-rows (d_toff, d_tadj; nullptr for an undirected graph).
+static int make_graph_from_device_csr(int64_t* d_off, int32_t* d_adj, int32_t n, int64_t nnz, int64_t* d_toff,
+                                      int32_t* d_tadj, bfs_graph** out) {
   bfs_graph* g = new bfs_graph();
   g->n = n;
   g->nnz = nnz;
   g->d_off = d_off;
   g->d_adj = d_adj;
+  g->directed = d_toff != nullptr;
+  g->d_toff = g->directed ? d_toff : d_off;
+  g->d_tadj = g->directed ? d_tadj : d_adj;
   g->parts = 1;
   g->part_base = {0, (int64_t)n};
   cudaGetDevice(&g->device);
@@ -211,8 +217,9 @@ static int make_graph_from_device_csr(int64_t* d_off, int32_t* d_adj, int32_t n,
     return cuda_fail(err, "part table copy");
   }
   int rc = dev_alloc((void**)&g->d_dead, sizeof(uint32_t) * (((size_t)n + 31) / 32), "edgeless-vertex bitmap");
-  if (!rc) rc = compute_dead_bits(d_off, n, g->d_dead, nullptr);
-  if (!rc) rc = build_big_chunks(d_off, n, nnz, nullptr, &g->d_big, &g->nbig);
+  // no arc enters a dead vertex; the big-row chunks serve the batched pull, which scans in-rows
+  if (!rc) rc = compute_dead_bits(g->d_toff, n, g->d_dead, nullptr);
+  if (!rc) rc = build_big_chunks(g->d_toff, n, nnz, nullptr, &g->d_big, &g->nbig);
   if (!rc) {
     err = cudaDeviceSynchronize();
     if (err != cudaSuccess) rc = cuda_fail(err, "edgeless-vertex bitmap");
@@ -262,9 +269,10 @@ int bfs_graph_create(const int64_t* offsets, const int32_t* adj, int32_t n, int6
     cudaFree(d_adj);
     return cuda_fail(err, "bfs_graph_create: copy");
   }
+  const bool directed = (flags & BFS_DIRECTED) != 0;
   if (flags & BFS_VALIDATE) {
     int ok = 0;
-    if (int e = validate_csr(d_off, d_adj, n, nnz, nullptr, &ok)) {
+    if (int e = validate_csr(d_off, d_adj, n, nnz, !directed, nullptr, &ok)) {
       cudaFree(d_off);
       cudaFree(d_adj);
       return e;
@@ -275,7 +283,23 @@ int bfs_graph_create(const int64_t* offsets, const int32_t* adj, int32_t n, int6
       return fail(BFS_ERR_INVALID_GRAPH, "bfs_graph_create: CSR failed validation (offsets, ids, order, loops or symmetry)");
     }
   }
-  return make_graph_from_device_csr(d_off, d_adj, n, nnz, out);
+  int64_t* d_toff = nullptr;
+  int32_t* d_tadj = nullptr;
+  if (directed) {
+    if (int e = build_transpose(d_off, d_adj, n, nnz, nullptr, &d_toff, &d_tadj)) {
+      cudaFree(d_off);
+      cudaFree(d_adj);
+      return e;
+    }
+  }
+  const int rc = make_graph_from_device_csr(d_off, d_adj, n, nnz, d_toff, d_tadj, out);
+  if (rc) {
+    cudaFree(d_off);
+    cudaFree(d_adj);
+    if (d_toff) cudaFree(d_toff);
+    if (d_tadj) cudaFree(d_tadj);
+  }
+  return rc;
 }
 
 int bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, uint32_t flags,
@@ -305,10 +329,28 @@ int bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, int64_t 
   int64_t* d_off = nullptr;
   int32_t* d_adj = nullptr;
   int64_t nnz = 0;
-  int rc = build_csr_from_edges(d_src, d_dst, m, n, s, &d_off, &d_adj, &nnz);
+  const bool directed = (flags & BFS_DIRECTED) != 0;
+  int rc = build_csr_from_edges(d_src, d_dst, m, n, directed ? 1 : 0, s, &d_off, &d_adj, &nnz);
+  int64_t* d_toff = nullptr;
+  int32_t* d_tadj = nullptr;
+  int64_t tnnz = 0;
+  if (!rc && directed) {
+    rc = build_csr_from_edges(d_src, d_dst, m, n, 2, s, &d_toff, &d_tadj, &tnnz);
+    if (rc) {
+      cudaFree(d_off);
+      cudaFree(d_adj);
+    }
+  }
   if (tmp) cudaFree(tmp);
   if (rc) return rc;
-  return make_graph_from_device_csr(d_off, d_adj, n, nnz, out);
+  rc = make_graph_from_device_csr(d_off, d_adj, n, nnz, d_toff, d_tadj, out);
+  if (rc) {
+    cudaFree(d_off);
+    cudaFree(d_adj);
+    if (d_toff) cudaFree(d_toff);
+    if (d_tadj) cudaFree(d_tadj);
+  }
+  return rc;
 }
 
 int bfs_graph_union(bfs_graph* const* graphs, int32_t count, void* stream, bfs_graph** out) {
@@ -318,6 +360,7 @@ int bfs_graph_union(bfs_graph* const* graphs, int32_t count, void* stream, bfs_g
   int64_t nnz = 0;
   for (int i = 0; i < count; ++i) {
     if (!graphs[i]) return fail(BFS_ERR_INVALID_ARG, "bfs_graph_union: NULL part");
+    if (graphs[i]->directed) return fail(BFS_ERR_UNSUPPORTED, "bfs_graph_union: directed parts are not supported");
     base[i + 1] = base[i] + graphs[i]->n;
     nnz += graphs[i]->nnz;
   }
@@ -355,7 +398,7 @@ int bfs_graph_union(bfs_graph* const* graphs, int32_t count, void* stream, bfs_g
     return rc;
   }
   bfs_graph* u = nullptr;
-  if (int e = make_graph_from_device_csr(d_off, d_adj, n, nnz, &u)) {
+  if (int e = make_graph_from_device_csr(d_off, d_adj, n, nnz, nullptr, nullptr, &u)) {
     cudaFree(d_off);
     cudaFree(d_adj);
     return e;
@@ -408,6 +451,10 @@ void bfs_graph_destroy(bfs_graph* g) {
   g->ws.clear();
   if (g->d_off) cudaFree(g->d_off);
   if (g->d_adj) cudaFree(g->d_adj);
+  if (g->directed) {
+    cudaFree(g->d_toff);
+    cudaFree(g->d_tadj);
+  }
   if (g->d_part_base) cudaFree(g->d_part_base);
   if (g->d_dead) cudaFree(g->d_dead);
   if (g->d_big) cudaFree(g->d_big);

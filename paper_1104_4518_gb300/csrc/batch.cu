@@ -53,8 +53,11 @@ constexpr int kBWarps = kBBlock / 32;
 constexpr int kShortRow = 32;  // rows up to this length are scanned by one lane
 
 struct BatchParams {
-  const int64_t* __restrict__ off;
+  const int64_t* __restrict__ off;   // out-rows: top-down
   const int32_t* __restrict__ adj;
+  const int64_t* __restrict__ toff;  // in-rows: pull (the same arrays when undirected)
+  const int32_t* __restrict__ tadj;
+  int32_t directed;
   int32_t n;
   long long nnz;
   int32_t k;  // roots in this traversal (<= 64)
@@ -69,7 +72,7 @@ struct BatchParams {
   void* V;     // Word[n]
   int32_t* queue[3];
   int64_t* chunks[2];
-  const int64_t* big;  // chunks of rows longer than kChunkEdges (static, per graph)
+  const int64_t* big;  // chunks of in-rows longer than kChunkEdges (static, per graph)
   long long nbig;
   LevelCtr* ctr;
   bfsdev::GridBarrier* bar;
@@ -131,7 +134,7 @@ __device__ __forceinline__ uint64_t resolve_lane(const BatchParams& p, const Wor
     int u[4];
     uint64_t f[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) u[q] = (j - q >= b) ? __ldg(&p.adj[j - q]) : -1;
+    for (int q = 0; q < 4; ++q) u[q] = (j - q >= b) ? __ldg(&p.tadj[j - q]) : -1;
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] = u[q] >= 0 ? (Bits)F[u[q]] : 0ull;
 #pragma unroll
@@ -163,7 +166,7 @@ __device__ __forceinline__ uint64_t resolve_warp(const BatchParams& p, const Wor
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const long long j = top - 1 - lane - 32 * q;
-      u[q] = j >= b ? __ldg(&p.adj[j]) : 0;
+      u[q] = j >= b ? __ldg(&p.tadj[j]) : 0;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) f[q] = (top - 1 - lane - 32 * q >= b) ? ((Bits)F[u[q]] & need) : 0ull;
@@ -369,8 +372,8 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         const int v = (int)(it >> 32);
         const uint64_t need = __shfl_sync(kFull, ~((Bits)V[v] | (Bits)Fc[v]) & p.mask, 0);
         if (!need) continue;
-        const long long rb = __ldg(&p.off[v]) + (it & 0xffffffffll) * kChunkEdges;
-        const long long re = min(rb + (long long)kChunkEdges, (long long)__ldg(&p.off[v + 1]));
+        const long long rb = __ldg(&p.toff[v]) + (it & 0xffffffffll) * kChunkEdges;
+        const long long re = min(rb + (long long)kChunkEdges, (long long)__ldg(&p.toff[v + 1]));
         pull_chunk(p, Fc, Fn, knext, v, rb, re, need, lane, cl, wq, nbuf);
       }
       // other rows: 32 vertices per warp; the owner lane updates V and F_{k+1}
@@ -385,8 +388,8 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
           fv = (Bits)Fc[v];
           need = ~(vv | fv) & p.mask;
           if (need) {
-            b = __ldg(&p.off[v]);
-            e = __ldg(&p.off[v + 1]);
+            b = __ldg(&p.toff[v]);
+            e = __ldg(&p.toff[v + 1]);
             if (e == b || e - b > kChunkEdges) need = 0;
           }
         }
@@ -394,7 +397,13 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         if (v0 < p.n) {
           const uint64_t nv = vv | fv | found;
           if (nv != vv) V[v] = (Word)nv;
-          if (found) Fn[v] = (Word)found;
+          if (found) {
+            Fn[v] = (Word)found;
+            if (p.directed) {  // the next level's top-down expansion needs the chunks of a long out-row
+              const long long deg = __ldg(&p.off[v + 1]) - __ldg(&p.off[v]);
+              if (deg > kChunkEdges) push_chunks_cta(p, knext, cl, v, deg);
+            }
+          }
         }
         warp_enqueue(p, knext, wq, nbuf, found != 0, v, lane, false);
       }
@@ -476,11 +485,16 @@ int launch_batch(const BatchRequest& r, cudaStream_t s) {
   if (r.width != 8 && r.width != 16 && r.width != 32 && r.width != 64)
     return fail(BFS_ERR_INVALID_ARG, "batch width must be 8, 16, 32 or 64");
   if (r.k < 1 || r.k > r.width) return fail(BFS_ERR_INVALID_ARG, "batch of 1..width roots expected");
+  if (!g->d_off || !g->d_toff || (g->nnz > 0 && (!g->d_adj || !g->d_tadj)))
+    return fail(BFS_ERR_INVALID_ARG, "graph without rows");
   if (int e = ensure_batch_state(g, w)) return e;
   const bfs_tuning t = effective_tuning(g);
   BatchParams p{};
   p.off = g->d_off;
   p.adj = g->d_adj;
+  p.toff = g->d_toff;
+  p.tadj = g->d_tadj;
+  p.directed = g->directed ? 1 : 0;
   p.n = g->n;
   p.nnz = g->nnz;
   p.k = r.k;

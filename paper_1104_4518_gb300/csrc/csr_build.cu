@@ -34,8 +34,10 @@ constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // ---------------- key emission ----------------
+// Keys of the arcs of edge e = (u, v): mode 0 (undirected) emits u -> v and
+// v -> u, mode 1 u -> v only, mode 2 v -> u only (the transpose).
 __global__ void make_keys_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                                 int32_t n, int vbits, uint64_t* __restrict__ keys,
+                                 int32_t n, int vbits, int mode, uint64_t* __restrict__ keys,
                                  unsigned long long* __restrict__ count, int* __restrict__ bad) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long mr = (m + 31) / 32 * 32;
@@ -51,13 +53,14 @@ __global__ void make_keys_kernel(const int32_t* __restrict__ src, const int32_t*
     }
     const unsigned bm = __ballot_sync(kFull, ok);
     if (!bm) continue;
+    const unsigned long long per = mode == 0 ? 2ull : 1ull;
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(count, 2ull * __popc(bm));
+    if (lane == 0) base = atomicAdd(count, per * __popc(bm));
     base = __shfl_sync(kFull, base, 0);
     if (ok) {
-      const unsigned long long at = base + 2ull * __popc(bm & bfsdev::lanemask_lt());
-      keys[at] = ((uint64_t)u << vbits) | (uint64_t)v;
-      keys[at + 1] = ((uint64_t)v << vbits) | (uint64_t)u;
+      const unsigned long long at = base + per * __popc(bm & bfsdev::lanemask_lt());
+      if (mode != 2) keys[at] = ((uint64_t)u << vbits) | (uint64_t)v;
+      if (mode != 1) keys[at + (mode == 0 ? 1 : 0)] = ((uint64_t)v << vbits) | (uint64_t)u;
     }
   }
 }
@@ -286,7 +289,7 @@ __global__ void fill_offsets_kernel(int64_t* off, int32_t n, long long value) {
 
 // ---------------- validation ----------------
 __global__ void validate_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ adj, int32_t n,
-                                long long nnz, int* __restrict__ bad) {
+                                long long nnz, int symmetric, int* __restrict__ bad) {
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const long long nwarps = (long long)gridDim.x * blockDim.x / 32;
@@ -303,6 +306,7 @@ __global__ void validate_kernel(const int64_t* __restrict__ off, const int32_t* 
         atomicExch(bad, 3);
         continue;
       }
+      if (!symmetric) continue;
       // symmetry: u must appear in v's row (binary search; v's row is checked by its own warp)
       long long lo = off[v], hi = off[v + 1];
       if (lo < 0 || hi > nnz || lo > hi) {
@@ -344,6 +348,19 @@ __global__ void dead_bits_kernel(const int64_t* __restrict__ off, int32_t n, lon
   }
 }
 
+// src[j] = u for every entry j of row u (one warp per row; entries outside
+// [0, nnz) of a malformed CSR are skipped).
+__global__ void expand_rows_kernel(const int64_t* __restrict__ off, int32_t n, long long nnz,
+                                   int32_t* __restrict__ src) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const long long nwarps = (long long)gridDim.x * blockDim.x / 32;
+  for (long long u = gw; u < n; u += nwarps) {
+    const long long b = max((long long)off[u], 0ll), e = min((long long)off[u + 1], nnz);
+    for (long long j = b + lane; j < e; j += 32) src[j] = (int32_t)u;
+  }
+}
+
 __global__ void big_chunks_kernel(const int64_t* __restrict__ off, int32_t n, int64_t* items,
                                   unsigned long long* count) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -364,8 +381,8 @@ int bits_for(int32_t n) {
 
 }  // namespace
 
-int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, cudaStream_t s,
-                         int64_t** d_off_out, int32_t** d_adj_out, int64_t* nnz_out) {
+int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, int mode,
+                         cudaStream_t s, int64_t** d_off_out, int32_t** d_adj_out, int64_t* nnz_out) {
   DeviceInfo di;
   if (int e = current_device_info(&di)) return e;
   const int vbits = bits_for(n);
@@ -381,7 +398,7 @@ int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, 
   int32_t* adj = nullptr;
   int rc = BFS_OK;
   long long N = 0, nnz = 0;
-  const long long cap = 2 * (long long)m;
+  const long long cap = (mode == 0 ? 2 : 1) * (long long)m;
   auto cleanup = [&]() {
     if (keys) cudaFree(keys);
     if (keys_alt) cudaFree(keys_alt);
@@ -404,7 +421,7 @@ int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, 
   if (cap > 0) {
     if ((rc = dev_alloc((void**)&keys, sizeof(uint64_t) * cap, "sort keys"))) return cleanup(), cudaFree(off), rc;
     const int grid = di.sm_count * 8;
-    make_keys_kernel<<<grid, 256, 0, s>>>(d_src, d_dst, m, n, vbits, keys, d_count, d_bad);
+    make_keys_kernel<<<grid, 256, 0, s>>>(d_src, d_dst, m, n, vbits, mode, keys, d_count, d_bad);
     int bad = 0;
     unsigned long long cnt = 0;
     err = cudaGetLastError();
@@ -522,7 +539,32 @@ int union_shift(int64_t* off, int32_t* adj, int64_t n_part, int64_t nnz_part, in
   return BFS_OK;
 }
 
-int validate_csr(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64_t nnz, cudaStream_t s, int* ok) {
+int build_transpose(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64_t nnz, cudaStream_t s,
+                    int64_t** d_toff, int32_t** d_tadj) {
+  DeviceInfo di;
+  if (int e = current_device_info(&di)) return e;
+  int32_t* src = nullptr;
+  if (int e = dev_alloc((void**)&src, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), "arc tails")) return e;
+  expand_rows_kernel<<<di.sm_count * 8, 256, 0, s>>>(d_off, n, nnz, src);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    cudaFree(src);
+    return cuda_fail(err, "arc tails");
+  }
+  int64_t tnnz = 0;
+  const int rc = build_csr_from_edges(src, d_adj, nnz, n, 2, s, d_toff, d_tadj, &tnnz);
+  cudaFree(src);
+  if (rc) return rc;
+  if (tnnz != nnz) {
+    cudaFree(*d_toff);
+    cudaFree(*d_tadj);
+    return fail(BFS_ERR_INVALID_GRAPH, "transpose: the CSR has repeated arcs or self-loops");
+  }
+  return BFS_OK;
+}
+
+int validate_csr(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64_t nnz, bool symmetric, cudaStream_t s,
+                 int* ok) {
   DeviceInfo di;
   if (int e = current_device_info(&di)) return e;
   int* d_bad = nullptr;
@@ -530,7 +572,7 @@ int validate_csr(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64_t 
   int bad = 0;
   cudaError_t err = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
   if (err == cudaSuccess) {
-    validate_kernel<<<di.sm_count * 4, 256, 0, s>>>(d_off, d_adj, n, nnz, d_bad);
+    validate_kernel<<<di.sm_count * 4, 256, 0, s>>>(d_off, d_adj, n, nnz, symmetric ? 1 : 0, d_bad);
     err = cudaGetLastError();
   }
   if (err == cudaSuccess) err = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);

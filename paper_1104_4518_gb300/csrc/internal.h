@@ -95,9 +95,12 @@ constexpr int kMaxSources = 4096;
 struct bfs_graph {
   int32_t n = 0;
   int64_t nnz = 0;
-  int64_t* d_off = nullptr;
+  int64_t* d_off = nullptr;   // rows of out-neighbours (all neighbours when undirected)
   int32_t* d_adj = nullptr;
-  uint32_t* d_dead = nullptr;  // bitmap of vertices without edges (tail bits set)
+  bool directed = false;
+  int64_t* d_toff = nullptr;  // rows of in-neighbours: the transpose when directed, else d_off
+  int32_t* d_tadj = nullptr;
+  uint32_t* d_dead = nullptr;  // bitmap of vertices no arc enters (tail bits set)
   int64_t* d_big = nullptr;    // (v << 32 | c) for every kChunkEdges-entry chunk c of rows longer than kChunkEdges
   int64_t nbig = 0;
   int32_t parts = 1;
@@ -124,8 +127,12 @@ bfs_tuning effective_tuning(const bfs_graph* g);
 
 // ---------------- kernels (launchers) ----------------
 // CSR construction from an edge list (device pointers).  Allocates d_off/d_adj.
-int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n,
+// mode 0: undirected (both arcs of every edge), 1: arcs src -> dst, 2: arcs dst -> src.
+int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, int mode,
                          cudaStream_t s, int64_t** d_off, int32_t** d_adj, int64_t* nnz);
+// The transpose of a directed CSR (row v lists the tails u of the arcs u -> v).
+int build_transpose(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64_t nnz, cudaStream_t s,
+                    int64_t** d_toff, int32_t** d_tadj);
 // Bitmap of the vertices without edges (bits beyond n set), one word per 32 vertices.
 int compute_dead_bits(const int64_t* d_off, int32_t n, uint32_t* d_dead, cudaStream_t s);
 // Chunk items of every row longer than kChunkEdges (order unspecified); *count receives their number.
@@ -134,7 +141,8 @@ int build_big_chunks(const int64_t* d_off, int32_t n, int64_t nnz, cudaStream_t 
 int union_shift(int64_t* off, int32_t* adj, int64_t n_part, int64_t nnz_part, int64_t off_shift, int32_t id_shift,
                 cudaStream_t s);
 // CSR validation on the device; *ok = 1 when valid.
-int validate_csr(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64_t nnz, cudaStream_t s, int* ok);
+int validate_csr(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64_t nnz, bool symmetric, cudaStream_t s,
+                 int* ok);
 
 struct RunRequest {
   bfs_graph* g = nullptr;

@@ -78,9 +78,12 @@ __device__ unsigned long long g_phase_ts[4096][8];
 #endif
 
 struct LoopParams {
-  const int64_t* __restrict__ off;
+  const int64_t* __restrict__ off;    // out-rows: top-down expansion
   const int32_t* __restrict__ adj;
-  const uint32_t* __restrict__ dead;  // vertices without edges (and the tail), or null
+  const int64_t* __restrict__ toff;   // in-rows: pull scans (the same arrays when undirected)
+  const int32_t* __restrict__ tadj;
+  int32_t directed;
+  const uint32_t* __restrict__ dead;  // vertices no arc enters (and the tail), or null
   int32_t n;
   int32_t nwords;
   long long nnz;
@@ -400,7 +403,8 @@ __device__ __forceinline__ void pull_finish(const LoopParams& p, uint32_t* nxt, 
   if (hit >= 0) {
     p.parent[v] = hit;
     p.level[v] = knext;
-    const long long deg = e - b;
+    // out-degree: the next level expands v's out-row (the row scanned here when undirected)
+    const long long deg = p.directed ? __ldg(&p.off[v + 1]) - __ldg(&p.off[v]) : e - b;
     acc_vertex(acc, deg);
     if (deg > p.chunk_deg) push_chunks_cta(p, knext, cl, v, deg);
   }
@@ -434,12 +438,12 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
     const bool a0 = live0 && !((visw0 >> lane) & 1u), a1 = live1 && !((visw1 >> lane) & 1u);
     long long b0 = 0, e0 = 0, b1 = 0, e1 = 0;
     if (a0) {
-      b0 = __ldg(&p.off[v0]);
-      e0 = __ldg(&p.off[v0 + 1]);
+      b0 = __ldg(&p.toff[v0]);
+      e0 = __ldg(&p.toff[v0 + 1]);
     }
     if (a1) {
-      b1 = __ldg(&p.off[v1]);
-      e1 = __ldg(&p.off[v1 + 1]);
+      b1 = __ldg(&p.toff[v1]);
+      e1 = __ldg(&p.toff[v1 + 1]);
     }
     const int P0 = a0 ? (int)min((long long)probe, e0 - b0) : 0;
     const int P1 = a1 ? (int)min((long long)probe, e1 - b1) : 0;
@@ -447,8 +451,8 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
     uint32_t x0[4], x1[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      u0[q] = q < P0 ? __ldg(&p.adj[e0 - 1 - q]) : 0;
-      u1[q] = q < P1 ? __ldg(&p.adj[e1 - 1 - q]) : 0;
+      u0[q] = q < P0 ? __ldg(&p.tadj[e0 - 1 - q]) : 0;
+      u1[q] = q < P1 ? __ldg(&p.tadj[e1 - 1 - q]) : 0;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -462,8 +466,8 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
       if (q < P1 && h1 < 0 && ((x1[q] >> (u1[q] & 31)) & 1u)) h1 = u1[q];
     }
     const long long t0 = e0 - P0, t1 = e1 - P1;
-    h0 = scan_desc_coop(p.adj, cur, b0, t0, a0 && h0 < 0 && t0 > b0, h0, lane);
-    h1 = scan_desc_coop(p.adj, cur, b1, t1, a1 && h1 < 0 && t1 > b1, h1, lane);
+    h0 = scan_desc_coop(p.tadj, cur, b0, t0, a0 && h0 < 0 && t0 > b0, h0, lane);
+    h1 = scan_desc_coop(p.tadj, cur, b1, t1, a1 && h1 < 0 && t1 > b1, h1, lane);
     if (live0) pull_finish(p, nxt, w0, vw0, visw0, v0, h0, b0, e0, knext, acc, sm.cl, wq, nbuf, lane);
     if (live1) pull_finish(p, nxt, w1, vw1, visw1, v1, h1, b1, e1, knext, acc, sm.cl, wq, nbuf, lane);
   }
@@ -563,7 +567,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   } else {  // dead bits from the row offsets, one warp per word
     const long long nv32 = (long long)p.nwords * 32;
     for (long long v = gtid; v < nv32; v += gthreads) {
-      const bool dead = v >= p.n || (single && v == s0) || __ldg(&p.off[v + 1]) == __ldg(&p.off[v]);
+      const bool dead = v >= p.n || (single && v == s0) || __ldg(&p.toff[v + 1]) == __ldg(&p.toff[v]);
       const unsigned dm = __ballot_sync(kFull, dead);
       if ((tid & 31) == 0) {
         const long long w = v >> 5;
@@ -698,7 +702,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
 
   if (gtid == 0) {
     p.misc[0] = k;
-    *p.edges_out = cum_edges / 2;
+    *p.edges_out = p.directed ? cum_edges : cum_edges / 2;  // arcs, or undirected edges
   }
   // ragged: copy the union-space outputs into each part's arrays, local ids
   if (p.part_out != nullptr) {
@@ -750,10 +754,15 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
     }
     BFS_CUDA_TRY(cudaEventRecord(w->stage_ev, s));
   }
+  if (!g->d_off || !g->d_toff || (g->nnz > 0 && (!g->d_adj || !g->d_tadj)))
+    return fail(BFS_ERR_INVALID_ARG, "graph without rows");
   const bfs_tuning t = effective_tuning(g);
   LoopParams p{};
   p.off = g->d_off;
   p.adj = g->d_adj;
+  p.toff = g->d_toff;
+  p.tadj = g->d_tadj;
+  p.directed = g->directed ? 1 : 0;
   p.dead = g->d_dead;
   p.n = g->n;
   p.nwords = w->nwords;

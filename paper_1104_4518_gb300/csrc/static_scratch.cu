@@ -87,6 +87,8 @@ extern "C" int bfs_run_static(const int64_t* offsets, const int32_t* adj, int32_
   g.nnz = nnz;
   g.d_off = const_cast<int64_t*>(offsets);
   g.d_adj = const_cast<int32_t*>(adj);
+  g.d_toff = g.d_off;  // undirected: the pull scans the same rows
+  g.d_tadj = g.d_adj;
   g.parts = 1;
   Workspace w;
   w.stream = s;
