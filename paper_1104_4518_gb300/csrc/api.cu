@@ -119,7 +119,7 @@ int get_workspace(bfs_graph* g, cudaStream_t s, Workspace** out) {
   if (!rc) rc = dev_alloc((void**)&w->vis, nb, "visited bitmap");
   for (int i = 0; i < 2 && !rc; ++i) rc = dev_alloc((void**)&w->chunks[i], sizeof(int64_t) * w->chunk_cap, "chunk items");
   if (!rc) rc = dev_alloc((void**)&w->ctr, sizeof(LevelCtr) * kCtrRing, "level counters");
-  if (!rc) rc = dev_alloc(&w->barrier, sizeof(bfsdev::GridBarrier), "grid barrier");
+  if (!rc) rc = dev_alloc(&w->barrier, 2 * sizeof(bfsdev::GridBarrier), "grid barriers");
   if (!rc) rc = dev_alloc((void**)&w->status, sizeof(int) * 4, "status");
   if (!rc) rc = dev_alloc((void**)&w->stats, sizeof(bfs_level_stat) * kMaxStatLevels, "level statistics");
   if (!rc) rc = dev_alloc((void**)&w->misc, sizeof(int32_t) * 16, "misc");
@@ -132,7 +132,7 @@ int get_workspace(bfs_graph* g, cudaStream_t s, Workspace** out) {
     if (e != cudaSuccess) rc = cuda_fail(e, "pinned staging");
   }
   if (!rc) {
-    cudaError_t e = cudaMemset(w->barrier, 0, sizeof(bfsdev::GridBarrier));
+    cudaError_t e = cudaMemset(w->barrier, 0, 2 * sizeof(bfsdev::GridBarrier));
     if (e == cudaSuccess) e = cudaMemset(w->status, 0, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMemset(w->ctr, 0, sizeof(LevelCtr) * kCtrRing);
     if (e != cudaSuccess) rc = cuda_fail(e, "workspace initialisation");
@@ -165,6 +165,16 @@ int ensure_batch_state(bfs_graph* g, Workspace* w) {
   return BFS_OK;
 }
 
+int prepare_barrier(Workspace* w, int kind, int grid, cudaStream_t s, bfsdev::GridBarrier** out) {
+  bfsdev::GridBarrier* bar = static_cast<bfsdev::GridBarrier*>(w->barrier) + kind;
+  if (w->bar_grid[kind] != grid) {
+    BFS_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(bfsdev::GridBarrier), s));
+    w->bar_grid[kind] = grid;
+  }
+  *out = bar;
+  return BFS_OK;
+}
+
 int stage_wait(Workspace* w) {
   BFS_CUDA_TRY(cudaEventSynchronize(w->stage_ev));
   return BFS_OK;
@@ -179,7 +189,8 @@ static int read_status(Workspace* w, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(e, "status read");
   if (st != 0) {
     cudaMemset(w->status, 0, sizeof(int));
-    cudaMemset(w->barrier, 0, sizeof(bfsdev::GridBarrier));
+    cudaMemset(w->barrier, 0, 2 * sizeof(bfsdev::GridBarrier));
+    w->bar_grid[0] = w->bar_grid[1] = 0;
     return fail(st, st == BFS_ERR_TIMEOUT ? "a device-side wait reached its limit; the traversal was abandoned"
                                           : "device reported an error");
   }

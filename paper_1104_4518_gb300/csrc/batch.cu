@@ -272,9 +272,9 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
   Word* V = static_cast<Word*>(p.V);
   __shared__ Claims cl;
   const int tid = threadIdx.x, lane = tid & 31;
-  unsigned epoch = 0;
+  unsigned long long bar_target = 0;
   if (tid == 0) {
-    epoch = bfsdev::ld_acquire_u32(&p.bar->epoch);
+    bar_target = bfsdev::barrier_base(p.bar, gridDim.x);
     claims_reset(cl);
   }
   const long long G = gridDim.x;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
   }
   if (blockIdx.x == 0 && tid < kCtrRing * (int)(sizeof(LevelCtr) / 8))
     reinterpret_cast<unsigned long long*>(p.ctr)[tid] = 0ull;
-  if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+  if (!bfsdev::grid_barrier(p.bar, nblocks, bar_target, p.spin_limit, p.status)) return;
 
   // seed: root r sets bit r of its own vertex (roots may repeat)
   if (blockIdx.x == 0 && tid < p.k) {
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
       if (deg > kChunkEdges) push_chunks(p, 0, s, deg);
     }
   }
-  if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+  if (!bfsdev::grid_barrier(p.bar, nblocks, bar_target, p.spin_limit, p.status)) return;
 
   int k = 0;
   uint64_t t_prev = 0;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
       warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
     }
     flush_claims(p, knext, cl);
-    if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+    if (!bfsdev::grid_barrier(p.bar, nblocks, bar_target, p.spin_limit, p.status)) return;
     if (p.stats && blockIdx.x == 0 && tid == 0 && k < kMaxStatLevels) {
       const uint64_t t = bfsdev::global_timer_ns();
       bfs_level_stat st{};
@@ -515,7 +515,6 @@ int launch_batch(const BatchRequest& r, cudaStream_t s) {
   p.big = g->d_big;
   p.nbig = g->nbig;
   p.ctr = w->ctr;
-  p.bar = reinterpret_cast<bfsdev::GridBarrier*>(w->barrier);
   p.status = w->status;
   p.misc = w->misc;
   p.stats = r.want_stats ? w->stats : nullptr;
@@ -528,8 +527,10 @@ int launch_batch(const BatchRequest& r, cudaStream_t s) {
   int per_sm = 0;
   BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBBlock, 0));
   if (per_sm < 1) return fail(BFS_ERR_CUDA, "batch kernel cannot be resident");
+  const int grid = per_sm * di.sm_count;
+  if (int e = prepare_barrier(w, 1, grid, s, &p.bar)) return e;
   void* args[] = {&p};
-  BFS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(per_sm * di.sm_count), dim3(kBBlock), args, 0, s));
+  BFS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBBlock), args, 0, s));
   return BFS_OK;
 }
 

@@ -11,14 +11,22 @@ namespace bfsdev {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Barrier words in global memory, 128-byte aligned so that the arrival
-// counter and the release epoch sit in separate L2 sectors.
+// Barrier word in global memory: a 64-bit arrival counter that only grows
+// (128-byte aligned, alone in its L2 line).
 struct __align__(128) GridBarrier {
-  unsigned count;
-  unsigned pad0[31];
-  unsigned epoch;
-  unsigned pad1[31];
+  unsigned long long count;
+  unsigned pad[30];
 };
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -49,41 +57,51 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Every
-// wait is bounded: after `spin_limit` polls (or once another CTA has posted an
-// error) the CTA records BFS_ERR_TIMEOUT in *status and the barrier returns
-// false, so that the kernel can return instead of hanging.  `epoch` is the
-// CTA's copy of the release counter (read once at kernel start).
-// Ordering: __syncthreads + a gpu-scope fence by thread 0 publish the CTA's
-// writes before its arrival; the acquire load that sees the new epoch, then
-// __syncthreads, order the CTA's later reads after every CTA's writes.
-__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned nblocks, unsigned& epoch,
+// CTA adds one to the arrival counter without waiting for the result and
+// polls until the counter reaches its target, nblocks more than at the
+// previous barrier: no CTA has to learn that it came last and publish a
+// release, which saves a round trip to L2 per barrier.
+// `target` is thread 0's copy of the count the barrier waits for; it starts
+// at barrier_base().  Every wait is bounded: after `spin_limit` polls (or once
+// another CTA has posted an error) the CTA records BFS_ERR_TIMEOUT in *status
+// and the barrier returns false, so that the kernel can return instead of
+// hanging.
+// Ordering: __syncthreads + a gpu-scope fence and the release add by thread 0
+// publish the CTA's writes before its arrival; the acquire load that sees the
+// target, then __syncthreads, order the CTA's later reads after every CTA's
+// writes.
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned nblocks, unsigned long long& target,
                                              unsigned spin_limit, int* status) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned target = epoch + 1;
+    target += nblocks;
     __threadfence();
-    const unsigned arrived = atom_add_acqrel_u32(&bar->count, 1u);
-    if (arrived == nblocks - 1) {
-      bar->count = 0;  // nobody arrives at the next barrier before the release below
-      st_release_u32(&bar->epoch, target);
-    } else {
-      unsigned polls = 0;
-      while (ld_acquire_u32(&bar->epoch) != target) {
-        if (++polls > spin_limit || ld_relaxed_i32(status) != 0) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    red_release_add_u64(&bar->count, 1ull);
+    unsigned polls = 0;
+    while (ld_acquire_u64(&bar->count) < target) {
+      if (++polls > spin_limit || ld_relaxed_i32(status) != 0) {
+        ok = 0;
+        break;
       }
+      __nanosleep(32);
     }
     if (!ok) atomicCAS(status, 0, (int)BFS_ERR_TIMEOUT);
-    epoch = target;
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// The count at which this launch's barriers start, read by thread 0 at kernel
+// start.  Every launch that used the word before ended on a multiple of
+// nblocks (the host zeroes the word when a kernel's grid size changes, and
+// after an error), and until this CTA arrives fewer than nblocks arrivals of
+// this launch can have happened, so rounding down gives the exact base.
+__device__ __forceinline__ unsigned long long barrier_base(const GridBarrier* bar, unsigned nblocks) {
+  const unsigned long long c = ld_acquire_u64(&bar->count);
+  return c - c % nblocks;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

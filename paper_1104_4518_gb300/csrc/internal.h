@@ -10,6 +10,10 @@
 
 #include "bfs.h"
 
+namespace bfsdev {
+struct GridBarrier;
+}
+
 namespace bfsint {
 
 // ---------------- error reporting ----------------
@@ -64,7 +68,8 @@ struct Workspace {
   int64_t* chunks[2] = {nullptr, nullptr};
   int64_t chunk_cap = 0;
   LevelCtr* ctr = nullptr;
-  void* barrier = nullptr;  // bfsdev::GridBarrier
+  void* barrier = nullptr;  // bfsdev::GridBarrier[2]: level loop, batched kernel
+  int bar_grid[2] = {0, 0};  // grid size of each kernel's last launch (host side)
   int* status = nullptr;
   bfs_level_stat* stats = nullptr;  // device, kMaxStatLevels
   int32_t* misc = nullptr;          // [0] level count, [1..] spare
@@ -160,6 +165,9 @@ struct RunRequest {
   // ragged: scatter union outputs into per-part outputs (device table of 2*parts pointers)
   int32_t** part_out = nullptr;
 };
+// The grid barrier of kernel `kind` (0: level loop, 1: batched) in w, zeroed
+// on the stream first when that kernel's grid size differs from its last launch.
+int prepare_barrier(Workspace* w, int kind, int grid, cudaStream_t s, bfsdev::GridBarrier** out);
 int launch_level_loop(const RunRequest& r, cudaStream_t s);
 
 struct BatchRequest {

@@ -507,9 +507,9 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   __shared__ Smem sm;
   extern __shared__ __align__(16) float s_mlp[];  // BFS_MLP_PARAMS floats when the learned selector is on
   const int tid = threadIdx.x;
-  unsigned epoch = 0;
+  unsigned long long bar_target = 0;
   if (tid == 0) {
-    epoch = bfsdev::ld_acquire_u32(&p.bar->epoch);
+    bar_target = bfsdev::barrier_base(p.bar, gridDim.x);
     sm.owner = -1;
     claims_reset(sm.cl);
     sm.acc[0] = sm.acc[1] = sm.acc[2] = sm.acc[3] = 0;
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
       if (deg > p.chunk_deg) push_chunks(p, 0, s0, deg);
     }
   }
-  if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+  if (!bfsdev::grid_barrier(p.bar, nblocks, bar_target, p.spin_limit, p.status)) return;
 
   if (!single) {  // seed level 0 with the sources (block 0)
     if (blockIdx.x == 0) {
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
       if (tid == 0) p.ctr[0].count = (unsigned)p.nsources;
       end_phase(p, 0, acc, sm);
     }
-    if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+    if (!bfsdev::grid_barrier(p.bar, nblocks, bar_target, p.spin_limit, p.status)) return;
   }
 
   // ---- level loop
@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
     end_phase(p, k + 1, acc, sm);
     PHASE_TS(k, 4);
     PHASE_ARRIVAL(k);
-    if (!bfsdev::grid_barrier(p.bar, nblocks, epoch, p.spin_limit, p.status)) return;
+    if (!bfsdev::grid_barrier(p.bar, nblocks, bar_target, p.spin_limit, p.status)) return;
     PHASE_TS(k, 6);
 
     if (p.want_stats && blockIdx.x == 0 && tid == 0 && k < kMaxStatLevels) {
@@ -777,7 +777,6 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   p.chunks[0] = w->chunks[0];
   p.chunks[1] = w->chunks[1];
   p.ctr = w->ctr;
-  p.bar = reinterpret_cast<bfsdev::GridBarrier*>(w->barrier);
   p.status = w->status;
   p.stats = w->stats;
   p.misc = w->misc;
@@ -816,6 +815,7 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_loop_kernel, kBlock, dyn_smem));
   if (per_sm < 1) return fail(BFS_ERR_CUDA, "level loop kernel cannot be resident");
   const int grid = per_sm * di.sm_count;
+  if (int e = prepare_barrier(w, 0, grid, s, &p.bar)) return e;
   p.small_frontier = t.small_frontier > 0 ? t.small_frontier : (t.small_frontier == 0 ? (long long)grid * kWarps : 0);
 #ifdef BFS_PHASE_TIMING
   fprintf(stderr, "level loop: %d CTAs (%d per SM), %zu bytes dynamic shared memory\n", grid, per_sm, dyn_smem);
