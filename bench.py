@@ -161,8 +161,6 @@ def measured_hbm_peak():
 
 def profile_traffic(name: str):
     """Per-launch DRAM traffic from a committed ncu summary, if it matches the current kernel source."""
-    import hashlib
-
     path = os.path.join(ROOT, "profiles", name)
     try:
         text = open(path).read()
