@@ -240,10 +240,12 @@ BFS_API int bfs_run_ragged(bfs_graph* u, const int32_t* sources, int32_t* const*
  * n <= 1,048,576 and nnz <= 67,108,864, beyond which the call returns
  * BFS_ERR_INVALID_ARG.  The first call on a device sets up that device (looks
  * up the array's device address and clears its barrier and status words), so
- * it should come before any stream capture.  Every call shares the array and
- * finds the previous call's contents there (the traversal re-initialises what
- * it needs), so calls that overlap on the GPU race: issue one at a time per
- * device.  The call waits for `stream` to finish the traversal and returns its
+ * it should come before any stream capture.  Every call zeroes the array's
+ * barrier word on `stream` (a memset, no allocation) before its launch.
+ * Every call shares the array and finds the previous call's contents there
+ * (the traversal re-initialises what it needs), so calls that overlap on the
+ * GPU race: issue one at a time per device.  Undirected graphs only (a
+ * directed graph needs bfs_graph_create with BFS_DIRECTED).  The call waits for `stream` to finish the traversal and returns its
  * device status (BFS_ERR_TIMEOUT if a device-side wait reached its limit).
  */
 BFS_API int bfs_run_static(const int64_t* offsets, const int32_t* adj, int32_t n, int64_t nnz, int32_t source,

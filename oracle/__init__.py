@@ -66,6 +66,9 @@ def _load():
             lib.oracle_bfs_directed.argtypes = [i64p, i32p, ctypes.c_int32, ctypes.c_int32, i32p, i32p, i32p]
             lib.oracle_out_edges.restype = ctypes.c_int64
             lib.oracle_out_edges.argtypes = [i64p, i32p, ctypes.c_int32]
+            lib.oracle_validate_arcs.restype = ctypes.c_int64
+            lib.oracle_validate_arcs.argtypes = [i32p, i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i32p,
+                                                 i32p, i32p, i64p]
             lib.oracle_validate_edges.restype = ctypes.c_int64
             lib.oracle_validate_edges.argtypes = [i32p, i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i32p,
                                                   i32p, i32p, i64p]
@@ -213,6 +216,24 @@ def validate_edges(src, dst, n: int, s: int, level: np.ndarray, parent: np.ndarr
                                       _p(bad, ctypes.c_int64))
     if r < 0:
         raise ValueError("oracle_validate_edges: bad argument")
+    return bad
+
+
+def validate_arcs(src, dst, n: int, s: int, level: np.ndarray, parent: np.ndarray):
+    """Violations (a, b, c, d) of a directed BFS result against the arc list src -> dst
+    (see oracle_validate_arcs in bfs_oracle.c): all zero exactly when `level` are the
+    directed distances from s and `parent` the largest in-neighbours one level up."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    best = np.empty(n, dtype=np.int32)
+    bad = np.zeros(4, dtype=np.int64)
+    r = _load().oracle_validate_arcs(_p(src, ctypes.c_int32), _p(dst, ctypes.c_int32), int(src.shape[0]), n, int(s),
+                                     _p(level, ctypes.c_int32), _p(parent, ctypes.c_int32), _p(best, ctypes.c_int32),
+                                     _p(bad, ctypes.c_int64))
+    if r < 0:
+        raise ValueError("oracle_validate_arcs: bad argument")
     return bad
 
 

@@ -280,3 +280,43 @@ int64_t oracle_out_edges(const int64_t* offsets, const int32_t* level, int32_t n
     if (level[v] >= 0) sum += offsets[v + 1] - offsets[v];
   return sum;
 }
+
+/*
+ * O(m + n) check of a directed BFS result against an arc list (u -> v), the
+ * directed counterpart of oracle_validate_edges.  best: int32[n] scratch;
+ * bad[4] receives (a) a wrong source entry, (b) arcs u -> v with u reached and
+ * v unreached or level[v] > level[u] + 1, (c) reached v != s without an
+ * in-neighbour one level up, or with a parent other than the largest such
+ * in-neighbour, or at level 0, (d) unreached v with parent != -1 or a level
+ * below -1.  All four are zero exactly when level[] are the directed distances
+ * from s and parent[] follows the max-id rule: (b) bounds every level by the
+ * distance and closes the reached set under the arcs, (c) gives every reached
+ * vertex a path from s of its level's length.  Returns the total, -1 on a bad
+ * argument.
+ */
+int64_t oracle_validate_arcs(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, int32_t s,
+                             const int32_t* level, const int32_t* parent, int32_t* best, int64_t* bad) {
+  if (n <= 0 || s < 0 || s >= n || !level || !parent || !best || !bad || (m > 0 && (!src || !dst))) return -1;
+  for (int i = 0; i < 4; ++i) bad[i] = 0;
+  if (level[s] != 0 || parent[s] != s) bad[0] += 1;
+  for (int32_t v = 0; v < n; ++v) best[v] = -1;
+  for (int64_t e = 0; e < m; ++e) {
+    int32_t u = src[e], v = dst[e];
+    if (u < 0 || u >= n || v < 0 || v >= n) return -1;
+    if (u == v || level[u] < 0) continue;
+    if (level[v] < 0 || level[v] > level[u] + 1) {
+      bad[1] += 1;
+      continue;
+    }
+    if (level[v] == level[u] + 1 && u > best[v]) best[v] = u;
+  }
+  for (int32_t v = 0; v < n; ++v) {
+    if (v == s) continue;
+    if (level[v] >= 0) {
+      if (level[v] == 0 || best[v] < 0 || parent[v] != best[v]) bad[2] += 1;
+    } else if (parent[v] != -1 || level[v] < -1) {
+      bad[3] += 1;
+    }
+  }
+  return bad[0] + bad[1] + bad[2] + bad[3];
+}

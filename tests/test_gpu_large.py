@@ -36,19 +36,59 @@ def _validate_rows(el, roots, levels, parents):
         assert b.sum() == 0, (int(roots[i]), b.tolist())
 
 
-def test_rmat26_single_root_bench_configuration():
-    """R-MAT scale 26 (67 M vertices, 2.1 G CSR entries), graph seed 3 / roots 103, heuristic selector."""
+def test_rmat26_single_root_and_batched_bench_configuration():
+    """R-MAT scale 26 (67 M vertices, 2.1 G CSR entries), graph seed 3 / roots 103: two single-root
+    traversals (heuristic selector) and the bench's 64-root batched traversal.  The batched rows of
+    those two roots equal the single-root results on the device, and the last batched row is
+    validated on its own."""
     el, roots = inputs.workload_rmat(26, 64, graph_seed=3, root_seed=103)
     g = device_graph_from_edges(el)
-    picks = [int(roots[0]), int(roots[len(roots) // 2])]
-    levels, parents = [], []
-    for s in picks:
-        parent, level = bfs.run(g, s)
+    picks = [0, len(roots) // 2]
+    levels, parents, singles = [], [], []
+    for i in picks:
+        parent, level = bfs.run(g, int(roots[i]))
         bfs.bfs_sync(g)
+        singles.append((parent, level))
+    pb, lb = bfs.run_batch(g, [int(r) for r in roots])
+    bfs.bfs_sync(g)
+    for i, (parent, level) in zip(picks, singles):
+        assert torch.equal(pb[i], parent) and torch.equal(lb[i], level), f"batched row {i}"
         levels.append(level.cpu().numpy())
         parents.append(parent.cpu().numpy())
+    last = len(roots) - 1
+    levels.append(lb[last].cpu().numpy())
+    parents.append(pb[last].cpu().numpy())
+    del pb, lb, singles
     g.destroy()
-    _validate_rows(el, picks, levels, parents)
+    _validate_rows(el, [int(roots[i]) for i in picks + [last]], levels, parents)
+
+
+def test_directed_rmat22_validated():
+    """Directed R-MAT scale 22 (the generated pairs read as arcs, 67 M of them): two single-root
+    traversals and a 16-root batched traversal, validated arc by arc (`oracle.validate_arcs`)."""
+    el = inputs.rmat(22, 16, seed=33)
+    roots = [int(r) for r in inputs.roots(el, 16, 34)]
+    g = bfs.bfs_graph_create_from_edges(torch.from_numpy(el.src).cuda(), torch.from_numpy(el.dst).cuda(), el.n,
+                                        directed=True)
+    rows = []
+    for s in roots[:2]:
+        parent, level = bfs.run(g, s)
+        bfs.bfs_sync(g)
+        rows.append((s, level.cpu().numpy(), parent.cpu().numpy()))
+    pb, lb = bfs.run_batch(g, roots)
+    bfs.bfs_sync(g)
+    rows.append((roots[-1], lb[-1].cpu().numpy(), pb[-1].cpu().numpy()))
+    assert np.array_equal(lb[0].cpu().numpy(), rows[0][1]) and np.array_equal(pb[0].cpu().numpy(), rows[0][2])
+    g.destroy()
+
+    def one(r):
+        s, lv, pa = r
+        return oracle.validate_arcs(el.src, el.dst, el.n, s, lv, pa)
+
+    with ThreadPoolExecutor(max_workers=len(rows)) as ex:
+        for (s, lv, _), b in zip(rows, ex.map(one, rows)):
+            assert b.sum() == 0, (s, b.tolist())
+            assert (lv > 0).sum() > 1000  # a real traversal, not a trivial one
 
 
 def test_rmat24_batched_64_roots():

@@ -149,3 +149,33 @@ def test_bad_arguments():
     g = oracle.digraph_csr(np.array([0], np.int32), np.array([1], np.int32), 3)
     with pytest.raises(ValueError):
         oracle.bfs_directed(g, 3)
+
+
+def test_arc_validator_accepts_the_oracle_and_rejects_planted_mistakes():
+    rng = np.random.default_rng(12)
+    n, m = 400, 1600
+    src, dst = rng.integers(0, n, m).astype(np.int32), rng.integers(0, n, m).astype(np.int32)
+    g = oracle.digraph_csr(src, dst, n)
+    for s in range(0, n, 53):
+        lv, pa, _ = oracle.bfs_directed(g, s)
+        assert oracle.validate_arcs(src, dst, n, s, lv, pa).sum() == 0
+    s = int(src[0])
+    lv, pa, _ = oracle.bfs_directed(g, s)
+    reached = np.nonzero((lv > 0))[0]
+    v = int(reached[len(reached) // 2])
+    bad = lv.copy(); bad[v] += 1                       # a level too deep
+    assert oracle.validate_arcs(src, dst, n, s, bad, pa).sum() > 0
+    bad = lv.copy(); bad[v] = -1                        # a reached vertex dropped
+    assert oracle.validate_arcs(src, dst, n, s, bad, pa).sum() > 0
+    wrong = pa.copy()                                   # a smaller in-neighbour one level up, if any
+    ins = [u for u, w in zip(src, dst) if w == v and u != v and lv[u] == lv[v] - 1]
+    if len(set(ins)) > 1:
+        wrong[v] = min(ins)
+        assert oracle.validate_arcs(src, dst, n, s, lv, wrong)[2] == 1
+    unreached = np.nonzero(lv < 0)[0]
+    if unreached.size:
+        wrong = pa.copy(); wrong[unreached[0]] = s       # an unreached vertex with a parent
+        assert oracle.validate_arcs(src, dst, n, s, lv, wrong)[3] == 1
+    # the undirected reading of the same arcs is not the directed result
+    lu, pu, _ = oracle.bfs(oracle.csr(src, dst, n), s)
+    assert oracle.validate_arcs(src, dst, n, s, lu, pu).sum() > 0
