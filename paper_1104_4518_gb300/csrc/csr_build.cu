@@ -270,6 +270,10 @@ __global__ void emit_csr_kernel(const uint64_t* __restrict__ keys, const int64_t
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
     const uint64_t k = keys[i];
+    // the rows after the last key's row end at nnz (the last key may repeat an
+    // earlier one, so this cannot wait for a first occurrence)
+    if (i == N - 1)
+      for (long long r = (long long)(k >> vbits) + 1; r <= n; ++r) off[r] = nnz;
     const bool first = (i == 0) || k != keys[i - 1];
     if (!first) continue;
     const long long p = pos[i];
@@ -277,8 +281,6 @@ __global__ void emit_csr_kernel(const uint64_t* __restrict__ keys, const int64_t
     const long long u = (long long)(k >> vbits);
     const long long pu = (i == 0) ? -1 : (long long)(keys[i - 1] >> vbits);
     for (long long r = pu + 1; r <= u; ++r) off[r] = p;
-    if (i == N - 1)
-      for (long long r = u + 1; r <= n; ++r) off[r] = nnz;
   }
 }
 
