@@ -133,8 +133,11 @@ typedef struct bfs_graph bfs_graph;
  * inputs.  With BFS_VALIDATE the copy is checked on the device (offsets
  * monotone from 0 to nnz, ids in range, rows strictly ascending, no
  * self-loops, symmetric) and BFS_ERR_INVALID_GRAPH is returned if it fails.
- * Without it a malformed CSR gives unspecified (but memory-safe for in-range
- * ids) results.  Requires 1 <= n < 2^31 - 1 and 0 <= nnz < 2^40.
+ * Without it, a CSR whose offsets are non-decreasing from 0 to nnz and whose
+ * ids lie in [0, n) but that breaks the other rules (order, repeats, loops,
+ * symmetry) gives unspecified but memory-safe results; offsets or ids outside
+ * those ranges may read out of bounds.  Requires 1 <= n < 2^31 - 1 and
+ * 0 <= nnz < 2^40.
  *
  * With BFS_DIRECTED the CSR holds the arcs of a directed graph: row u lists the
  * heads v of the arcs u -> v (sorted, no repeats, no self-loops; symmetry is
