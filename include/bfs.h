@@ -98,7 +98,7 @@ typedef struct bfs_tuning {
   int32_t chunk_degree;  /* top-down: vertices above this degree are split into grid-wide chunks of 1024
                             edges (>= 1024, default 1024) */
   float alpha;           /* heuristic: go PULL when frontier edges * alpha' > unvisited edges and the
-                            frontier grows, alpha' = alpha * (1 + 4 n / L2 bytes) (default 30) */
+                            frontier grows, alpha' = alpha * (1 + 4 n / L2 bytes) (default 20) */
   float beta;            /* heuristic: leave PULL when frontier count < n / beta (default 24) */
   int32_t batch_topdown_limit; /* batched: levels with at most this many active vertices expand top-down (default n/64) */
   int32_t small_frontier; /* heuristic: a top-down level whose frontier has at most this many vertices, none of

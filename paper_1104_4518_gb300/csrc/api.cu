@@ -79,7 +79,7 @@ bfs_tuning effective_tuning(const bfs_graph* g) {
   if (t.pull_thread_degree > 4) t.pull_thread_degree = 4;
   if (t.chunk_degree <= 0) t.chunk_degree = 1024;
   if (t.chunk_degree < kChunkEdges) t.chunk_degree = kChunkEdges;
-  if (!(t.alpha > 0.0f)) t.alpha = 30.0f;
+  if (!(t.alpha > 0.0f)) t.alpha = 20.0f;
   if (!(t.beta > 0.0f)) t.beta = 24.0f;
   if (t.batch_topdown_limit <= 0) t.batch_topdown_limit = std::max(1024, g->n / 64);
   if (t.batch_width != 8 && t.batch_width != 16 && t.batch_width != 32 && t.batch_width != 64) t.batch_width = 64;
@@ -784,7 +784,7 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
     const int cd[] = {128, 256, 1024};
     const int pd[] = {1, 2, 3, 4};
     const int ch[] = {1024, 2048, 4096};
-    const float al[] = {7.0f, 14.0f, 30.0f, 60.0f, 120.0f};
+    const float al[] = {10.0f, 14.0f, 20.0f, 30.0f, 45.0f};
     const float be[] = {8.0f, 16.0f, 24.0f, 48.0f, 96.0f};
     const int sf[] = {-1, 0, 2 * 4864, 4 * 4864};
     for (int knob = 0; knob < 7 && !rc; ++knob) {
