@@ -222,10 +222,14 @@ __device__ __forceinline__ void td_visit(const BatchParams& p, const Word* Fc, W
                                          uint64_t f, int u, int w, Claims& cl) {
   const uint64_t nb = f & ~((Bits)V[w] | (Bits)Fc[w]);
   if (!nb) return;
-  for (uint64_t b = nb; b;) {  // u is a parent candidate of w for every new root bit
+  // u is a parent candidate of w for every new root bit; an offer no larger than
+  // the current one is dropped without an atomic (the row of w is one 256-byte
+  // line, read once)
+  for (uint64_t b = nb; b;) {
     const int r = __ffsll((long long)b) - 1;
     b &= b - 1;
-    atomicMax(&p.sp[(long long)w * p.stride + r], u);
+    int32_t* o = &p.sp[(long long)w * p.stride + r];
+    if (__ldcg(o) < u) atomicMax(o, u);
   }
   if (((Bits)Fn[w] & nb) == nb) return;
   const Bits old = atomic_or_word(&Fn[w], nb);
