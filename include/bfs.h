@@ -52,8 +52,25 @@ typedef enum bfs_status {
   BFS_ERR_OOM = 3,           /* a device allocation failed */
   BFS_ERR_CUDA = 4,          /* a CUDA runtime call failed (message has the CUDA error) */
   BFS_ERR_TIMEOUT = 5,       /* a device-side wait hit its iteration limit; the run was abandoned */
-  BFS_ERR_UNSUPPORTED = 6    /* no CUDA device, or a device older than sm_103 */
+  BFS_ERR_UNSUPPORTED = 6,   /* no CUDA device, or a device older than sm_103 */
+  BFS_ERR_BOUNDS = 7         /* bounds-checking build only: an index outside its array (see below) */
 } bfs_status;
+
+/*
+ * The bounds-checking build (the same sources compiled with -DBFS_BOUNDS_CHECK,
+ * shipped beside the normal library as libbfs_gb300_checked.so) checks every
+ * index the traversal kernels take from the graph or from a counter before
+ * using it: each adjacency id against [0, n), each frontier-queue slot against
+ * n, each chunk-list slot against the list's capacity.  An index outside its
+ * range is not used; the first one is recorded with its site, and the call
+ * that reports the device status (bfs_sync, a synchronising run, the ragged
+ * or static entry points) returns BFS_ERR_BOUNDS with the site and the index
+ * in bfs_last_error().  Row offsets are checked where a graph is created, and
+ * by each bfs_run_static call (non-decreasing from 0 to nnz; BFS_ERR_BOUNDS
+ * otherwise), even without BFS_VALIDATE.  The normal build has none of these
+ * checks.  Results of a well-formed graph are identical in both builds.
+ */
+BFS_API int bfs_bounds_checked(void); /* 1 in the bounds-checking build, 0 otherwise */
 
 /* Flags of bfs_graph_create / bfs_graph_create_from_edges / bfs_opts.flags. */
 #define BFS_HOST_PTRS 0x1u /* the input (graph create) or output (run) pointers are host memory */
@@ -136,7 +153,8 @@ typedef struct bfs_graph bfs_graph;
  * Without it, a CSR whose offsets are non-decreasing from 0 to nnz and whose
  * ids lie in [0, n) but that breaks the other rules (order, repeats, loops,
  * symmetry) gives unspecified but memory-safe results; offsets or ids outside
- * those ranges may read out of bounds.  Requires 1 <= n < 2^31 - 1 and
+ * those ranges may read out of bounds (the bounds-checking build turns them
+ * into BFS_ERR_BOUNDS instead).  Requires 1 <= n < 2^31 - 1 and
  * 0 <= nnz < 2^40.
  *
  * With BFS_DIRECTED the CSR holds the arcs of a directed graph: row u lists the
@@ -194,8 +212,8 @@ BFS_API void bfs_graph_destroy(bfs_graph* g);
  * cooperative kernel launch per traversal: every level is an expansion phase
  * followed by a grid-wide barrier, with the level count held on the device.
  * Asynchronous unless opts asks for statistics or host outputs.  Device-side
- * failures (BFS_ERR_TIMEOUT) are returned by bfs_sync or by a synchronising
- * call; until then further runs on the same stream do no work.
+ * failures (BFS_ERR_TIMEOUT; BFS_ERR_BOUNDS in the bounds-checking build) are
+ * returned by bfs_sync or by a synchronising call; until then further runs on the same stream do no work.
  */
 BFS_API int bfs_run(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_out,
             const bfs_opts* opts, void* stream);
@@ -249,7 +267,8 @@ BFS_API int bfs_run_ragged(bfs_graph* u, const int32_t* sources, int32_t* const*
  * (the traversal re-initialises what it needs), so calls that overlap on the
  * GPU race: issue one at a time per device.  Undirected graphs only (a
  * directed graph needs bfs_graph_create with BFS_DIRECTED).  The call waits for `stream` to finish the traversal and returns its
- * device status (BFS_ERR_TIMEOUT if a device-side wait reached its limit).
+ * device status (BFS_ERR_TIMEOUT if a device-side wait reached its limit,
+ * BFS_ERR_BOUNDS from the bounds-checking build).
  */
 BFS_API int bfs_run_static(const int64_t* offsets, const int32_t* adj, int32_t n, int64_t nnz, int32_t source,
                            int32_t* parent_out, int32_t* level_out, void* stream);

@@ -21,7 +21,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libbfs_gb300.so")
+# BFS_BOUNDS_CHECK=1 in the environment selects the bounds-checking build
+# (every device index checked, BFS_ERR_BOUNDS) for the whole process.
+BOUNDS_CHECKED = os.environ.get("BFS_BOUNDS_CHECK", "0") == "1"
+LIB_PATH = os.path.join(_HERE, "libbfs_gb300_checked.so" if BOUNDS_CHECKED else "libbfs_gb300.so")
 
 BFS_OK = 0
 BFS_ERR_INVALID_ARG = 1
@@ -30,6 +33,7 @@ BFS_ERR_OOM = 3
 BFS_ERR_CUDA = 4
 BFS_ERR_TIMEOUT = 5
 BFS_ERR_UNSUPPORTED = 6
+BFS_ERR_BOUNDS = 7
 
 BFS_HOST_PTRS = 0x1
 BFS_VALIDATE = 0x2
@@ -116,6 +120,7 @@ def _declare(lib):
         "bfs_selector_load": [ctypes.c_char_p],
         "bfs_selector_save": [ctypes.c_char_p],
         "bfs_level_features": [i32, i64, i32, i64, i64, i64, i64, ctypes.POINTER(i64), ctypes.POINTER(f32)],
+        "bfs_bounds_checked": [],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -478,6 +483,11 @@ def bfs_level_features(n, nnz, k, frontier_count, frontier_edges, unvisited_coun
 
 def bfs_version() -> str:
     return lib().bfs_version().decode()
+
+
+def bfs_bounds_checked() -> bool:
+    """True when the loaded library is the bounds-checking build."""
+    return bool(lib().bfs_bounds_checked())
 
 
 # ---------------- conveniences over the C ABI ----------------

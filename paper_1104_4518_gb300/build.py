@@ -2,7 +2,9 @@
 
 Each .cu under csrc/ is compiled to an object in parallel, then the objects
 are linked into one shared library whose only interface is the C ABI of
-include/bfs.h.  No PyTorch headers or libraries are involved.
+include/bfs.h.  No PyTorch headers or libraries are involved.  build_all()
+also builds the bounds-checking library libbfs_gb300_checked.so (the same
+sources with -DBFS_BOUNDS_CHECK), at the same time.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbfs_gb300.so")
+CHECKED_LIB = os.path.join(PKG, "libbfs_gb300_checked.so")
+CHECKED_BUILD_DIR = os.path.join(PKG, "_build_checked")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-Xcompiler", "-fvisibility=hidden",
@@ -85,6 +89,22 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     return LIB_OUT
 
 
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """The bounds-checking library (every index checked on the device, BFS_ERR_BOUNDS)."""
+    return build(force=force, verbose=verbose, extra_flags=["-DBFS_BOUNDS_CHECK"], lib_path=CHECKED_LIB,
+                 build_dir=CHECKED_BUILD_DIR)
+
+
+def build_all(force: bool = False, verbose: bool = False) -> list[str]:
+    """Both libraries, compiled side by side."""
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        futs = [ex.submit(build, force, verbose), ex.submit(build_checked, force, verbose)]
+        return [f.result() for f in futs]
+
+
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv, ptxas_verbose="--ptxas" in sys.argv)
-    print(LIB)
+    if "--ptxas" in sys.argv:
+        build(force="--force" in sys.argv, verbose="-v" in sys.argv, ptxas_verbose=True)
+        print(LIB)
+    else:
+        print("\n".join(build_all(force="--force" in sys.argv, verbose="-v" in sys.argv)))

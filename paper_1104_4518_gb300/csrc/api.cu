@@ -180,19 +180,34 @@ int stage_wait(Workspace* w) {
   return BFS_OK;
 }
 
+// Message of a nonzero device status word quad (code, site, 64-bit index).
+std::string device_status_message(const int* st) {
+  if (st[0] == BFS_ERR_TIMEOUT) return "a device-side wait reached its limit; the traversal was abandoned";
+  if (st[0] == BFS_ERR_BOUNDS) {
+    static const char* const sites[] = {"?", "top-down adjacency id", "pull adjacency id", "frontier queue slot",
+                                        "chunk list slot", "batched top-down adjacency id",
+                                        "batched pull adjacency id"};
+    long long idx = 0;
+    std::memcpy(&idx, st + 2, sizeof(idx));
+    const int site = st[1] >= 1 && st[1] <= 6 ? st[1] : 0;
+    return std::string("bounds check failed: ") + sites[site] + " " + std::to_string(idx) +
+           " outside its range; the traversal was abandoned";
+  }
+  return "device reported an error";
+}
+
 // Reads (and clears) the device status of a workspace; resets the barrier on error.
 static int read_status(Workspace* w, cudaStream_t s) {
-  int st = 0;
+  int st[4] = {0, 0, 0, 0};
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronisation");
-  e = cudaMemcpy(&st, w->status, sizeof(int), cudaMemcpyDeviceToHost);
+  e = cudaMemcpy(st, w->status, sizeof(st), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "status read");
-  if (st != 0) {
-    cudaMemset(w->status, 0, sizeof(int));
+  if (st[0] != 0) {
+    cudaMemset(w->status, 0, sizeof(st));
     cudaMemset(w->barrier, 0, 2 * sizeof(bfsdev::GridBarrier));
     w->bar_grid[0] = w->bar_grid[1] = 0;
-    return fail(st, st == BFS_ERR_TIMEOUT ? "a device-side wait reached its limit; the traversal was abandoned"
-                                          : "device reported an error");
+    return fail(st[0], device_status_message(st));
   }
   return BFS_OK;
 }
@@ -206,6 +221,15 @@ static int check_graph(const bfs_graph* g) {
 // the in-rows (d_toff, d_tadj; nullptr for an undirected graph).
 static int make_graph_from_device_csr(int64_t* d_off, int32_t* d_adj, int32_t n, int64_t nnz, int64_t* d_toff,
                                       int32_t* d_tadj, bfs_graph** out) {
+  if (bfsdev::kBoundsCheck) {  // every row inside [0, nnz), so that the kernels only need to check ids
+    int* d_flag = nullptr;
+    if (int e = dev_alloc((void**)&d_flag, sizeof(int), "offset check flag")) return e;
+    int ok = 0, rc = check_offsets(d_off, n, nnz, d_flag, nullptr, &ok);
+    if (!rc && ok && d_toff) rc = check_offsets(d_toff, n, nnz, d_flag, nullptr, &ok);
+    cudaFree(d_flag);
+    if (rc) return rc;
+    if (!ok) return fail(BFS_ERR_BOUNDS, "bounds check failed: row offsets are not non-decreasing from 0 to nnz");
+  }
   bfs_graph* g = new bfs_graph();
   g->n = n;
   g->nnz = nnz;
@@ -254,7 +278,11 @@ extern "C" {
 
 const char* bfs_last_error(void) { return t_last_error.c_str(); }
 
-const char* bfs_version(void) { return "bfs_gb300 1.0 (sm_103a)"; }
+const char* bfs_version(void) {
+  return bfsdev::kBoundsCheck ? "bfs_gb300 1.0 (sm_103a, bounds-checking build)" : "bfs_gb300 1.0 (sm_103a)";
+}
+
+int bfs_bounds_checked(void) { return bfsdev::kBoundsCheck ? 1 : 0; }
 
 int bfs_graph_create(const int64_t* offsets, const int32_t* adj, int32_t n, int64_t nnz, uint32_t flags,
                      bfs_graph** out) {

@@ -72,6 +72,7 @@ struct BatchParams {
   void* V;     // Word[n]
   int32_t* queue[3];
   int64_t* chunks[2];
+  long long chunk_cap;  // entries of each chunk list
   const int64_t* big;  // chunks of in-rows longer than kChunkEdges (static, per graph)
   long long nbig;
   LevelCtr* ctr;
@@ -136,7 +137,12 @@ __device__ __forceinline__ uint64_t resolve_lane(const BatchParams& p, const Wor
 #pragma unroll
     for (int q = 0; q < 4; ++q) u[q] = (j - q >= b) ? __ldg(&p.tadj[j - q]) : -1;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] = u[q] >= 0 ? (Bits)F[u[q]] : 0ull;
+    for (int q = 0; q < 4; ++q) {
+      const bool live = bfsdev::kBoundsCheck
+                            ? j - q >= b && bfsdev::in_range(p.status, bfsdev::kSiteBatchPull, u[q], p.n)
+                            : u[q] >= 0;
+      f[q] = live ? (Bits)F[u[q]] : 0ull;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint64_t h = f[q] & need;
@@ -169,7 +175,10 @@ __device__ __forceinline__ uint64_t resolve_warp(const BatchParams& p, const Wor
       u[q] = j >= b ? __ldg(&p.tadj[j]) : 0;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[q] = (top - 1 - lane - 32 * q >= b) ? ((Bits)F[u[q]] & need) : 0ull;
+    for (int q = 0; q < 4; ++q)
+      f[q] = (top - 1 - lane - 32 * q >= b && bfsdev::in_range(p.status, bfsdev::kSiteBatchPull, u[q], p.n))
+                 ? ((Bits)F[u[q]] & need)
+                 : 0ull;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint64_t nb = warp_or<Word>(f[q]) & need;
@@ -220,6 +229,7 @@ __device__ __forceinline__ uint64_t resolve_group(const BatchParams& p, const Wo
 template <typename Word>
 __device__ __forceinline__ void td_visit(const BatchParams& p, const Word* Fc, Word* Fn, const Word* V, int knext,
                                          uint64_t f, int u, int w, Claims& cl) {
+  if (!bfsdev::in_range(p.status, bfsdev::kSiteBatchTopDown, w, p.n)) return;
   const uint64_t nb = f & ~((Bits)V[w] | (Bits)Fc[w]);
   if (!nb) return;
   // u is a parent candidate of w for every new root bit; an offer no larger than
@@ -516,6 +526,7 @@ int launch_batch(const BatchRequest& r, cudaStream_t s) {
   p.V = w->bvis;
   p.chunks[0] = w->chunks[0];
   p.chunks[1] = w->chunks[1];
+  p.chunk_cap = w->chunk_cap;
   p.big = g->d_big;
   p.nbig = g->nbig;
   p.ctr = w->ctr;

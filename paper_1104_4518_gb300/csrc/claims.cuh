@@ -9,7 +9,9 @@
 // in L2, cost more than the level's memory traffic.
 //
 // P is a kernel's parameter block with the fields ctr (LevelCtr ring), queue[3]
-// and chunks[2]; every function here expects 512-thread CTAs.
+// (n entries each), chunks[2] (chunk_cap entries each), n and status; every
+// function here expects 512-thread CTAs.  In the bounds-checking build every
+// queue and chunk-list slot is checked against its capacity before the write.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -91,7 +93,9 @@ __device__ __forceinline__ void push_chunks(const P& p, int knext, int v, long l
   if (g.thread_rank() == g.size() - 1) base = atomicAdd(&p.ctr[knext % kCtrRing].chunks, incl);
   const unsigned pos = g.shfl(base, g.size() - 1) + incl - nch;
   int64_t* dst = p.chunks[knext & 1];
-  for (unsigned c = 0; c < nch; ++c) dst[pos + c] = ((int64_t)v << 32) | (int64_t)c;
+  for (unsigned c = 0; c < nch; ++c)
+    if (bfsdev::in_range(p.status, bfsdev::kSiteChunk, (long long)pos + c, p.chunk_cap))
+      dst[pos + c] = ((int64_t)v << 32) | (int64_t)c;
 }
 
 // Records vertex v of level knext for chunking in the CTA's buffer; a full
@@ -120,7 +124,8 @@ __device__ __forceinline__ void cta_enqueue(const P& p, int knext, Claims& cl, i
     unsigned base = 0;
     if (g.thread_rank() == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)g.size());
     base = g.shfl(base, 0);
-    p.queue[knext % 3][base + g.thread_rank()] = w;
+    if (bfsdev::in_range(p.status, bfsdev::kSiteQueue, (long long)base + g.thread_rank(), p.n))
+      p.queue[knext % 3][base + g.thread_rank()] = w;
   }
 }
 
@@ -138,7 +143,8 @@ __device__ __forceinline__ void warp_enqueue(const P& p, int knext, int* wq, int
   unsigned base = 0;
   if (lane == 0) base = atomicAdd(&p.ctr[knext % kCtrRing].count, (unsigned)nbuf);
   base = __shfl_sync(bfsdev::kFull, base, 0);
-  for (int i = lane; i < nbuf; i += 32) p.queue[knext % 3][base + i] = wq[i];
+  for (int i = lane; i < nbuf; i += 32)
+    if (bfsdev::in_range(p.status, bfsdev::kSiteQueue, (long long)base + i, p.n)) p.queue[knext % 3][base + i] = wq[i];
   __syncwarp();
   nbuf = 0;
 }
@@ -168,7 +174,8 @@ __device__ __forceinline__ void flush_claims(const P& p, int knext, Claims& cl) 
   }
   __syncthreads();
   int32_t* Q = p.queue[knext % 3];
-  for (int i = threadIdx.x; i < nq; i += kClaimBlock) Q[cl.qbase + i] = cl.cq[i];
+  for (int i = threadIdx.x; i < nq; i += kClaimBlock)
+    if (bfsdev::in_range(p.status, bfsdev::kSiteQueue, (long long)cl.qbase + i, p.n)) Q[cl.qbase + i] = cl.cq[i];
   int64_t* dst = p.chunks[knext & 1];
   for (int it = threadIdx.x; it < nch_total; it += kClaimBlock) {
     int lo = 0, hi = nbig - 1;  // the first entry whose inclusive prefix exceeds it
@@ -178,7 +185,8 @@ __device__ __forceinline__ void flush_claims(const P& p, int knext, Claims& cl) 
       else lo = mid + 1;
     }
     const int c = it - (lo ? cl.bign[lo - 1] : 0);
-    dst[cl.bbase + it] = ((int64_t)cl.bigv[lo] << 32) | (int64_t)c;
+    if (bfsdev::in_range(p.status, bfsdev::kSiteChunk, (long long)cl.bbase + it, p.chunk_cap))
+      dst[cl.bbase + it] = ((int64_t)cl.bigv[lo] << 32) | (int64_t)c;
   }
   __syncthreads();
   if (threadIdx.x == 0) claims_reset(cl);

@@ -331,6 +331,15 @@ __global__ void validate_kernel(const int64_t* __restrict__ off, const int32_t* 
   }
 }
 
+// Row offsets non-decreasing from 0 to nnz (every row inside [0, nnz)).
+__global__ void offsets_kernel(const int64_t* __restrict__ off, int32_t n, long long nnz, int* __restrict__ bad) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i0 == 0 && (off[0] != 0 || off[n] != nnz)) atomicExch(bad, 1);
+  for (long long v = i0; v < n; v += stride)
+    if (off[v] > off[v + 1]) atomicExch(bad, 1);
+}
+
 __global__ void shift_kernel(int64_t* off, int32_t* adj, long long n_part, long long nnz_part, long long off_shift,
                              int32_t id_shift) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -562,6 +571,22 @@ int build_transpose(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64
     cudaFree(*d_tadj);
     return fail(BFS_ERR_INVALID_GRAPH, "transpose: the CSR has repeated arcs or self-loops");
   }
+  return BFS_OK;
+}
+
+int check_offsets(const int64_t* d_off, int32_t n, int64_t nnz, int* d_flag, cudaStream_t s, int* ok) {
+  DeviceInfo di;
+  if (int e = current_device_info(&di)) return e;
+  int bad = 0;
+  cudaError_t err = cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+  if (err == cudaSuccess) {
+    offsets_kernel<<<di.sm_count * 4, 256, 0, s>>>(d_off, n, nnz, d_flag);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&bad, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_fail(err, "row offset check");
+  *ok = bad == 0;
   return BFS_OK;
 }
 

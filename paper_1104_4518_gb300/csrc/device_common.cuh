@@ -11,6 +11,43 @@ namespace bfsdev {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// The bounds-checking build (-DBFS_BOUNDS_CHECK) checks every index that the
+// traversal kernels take from the graph or from a counter before using it.
+#ifdef BFS_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+
+// Where an index was checked (status[1] of a bounds error).
+enum BoundsSite : int {
+  kSiteTopDown = 1,       // adjacency id of a top-down expansion (single-source kernel)
+  kSitePull = 2,          // adjacency id of a pull scan (single-source kernel)
+  kSiteQueue = 3,         // slot of the next frontier queue
+  kSiteChunk = 4,         // slot of the chunk list
+  kSiteBatchTopDown = 5,  // adjacency id of a top-down expansion (batched kernel)
+  kSiteBatchPull = 6,     // adjacency id of a pull scan (batched kernel)
+};
+
+// True when 0 <= i < cap.  In the bounds-checking build an index outside that
+// range makes the first such thread record BFS_ERR_BOUNDS in status[0], the
+// site in status[1] and the index in status[2..3] (as one 64-bit word; status
+// is 16-byte aligned), and returns false so that the caller skips the access.
+// The other CTAs see the status at their next grid barrier and return.  In the
+// normal build it is always true and costs nothing.
+__device__ __forceinline__ bool in_range(int* status, BoundsSite site, long long i, long long cap) {
+  if constexpr (!kBoundsCheck) {
+    return true;
+  } else {
+    if (i >= 0 && i < cap) return true;
+    if (atomicCAS(status, 0, (int)BFS_ERR_BOUNDS) == 0) {
+      status[1] = (int)site;
+      *reinterpret_cast<long long*>(status + 2) = i;
+    }
+    return false;
+  }
+}
+
 // Barrier word in global memory: a 64-bit arrival counter that only grows
 // (128-byte aligned, alone in its L2 line).
 struct __align__(128) GridBarrier {

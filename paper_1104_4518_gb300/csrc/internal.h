@@ -135,6 +135,11 @@ bfs_tuning effective_tuning(const bfs_graph* g);
 // mode 0: undirected (both arcs of every edge), 1: arcs src -> dst, 2: arcs dst -> src.
 int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, int mode,
                          cudaStream_t s, int64_t** d_off, int32_t** d_adj, int64_t* nnz);
+// Message of a nonzero device status (status[0] code, [1] site, [2..3] index).
+std::string device_status_message(const int* status4);
+// Row offsets non-decreasing from 0 to nnz?  d_flag: one device int of scratch.
+// Synchronises s.
+int check_offsets(const int64_t* d_off, int32_t n, int64_t nnz, int* d_flag, cudaStream_t s, int* ok);
 // The transpose of a directed CSR (row v lists the tails u of the arcs u -> v).
 int build_transpose(const int64_t* d_off, const int32_t* d_adj, int32_t n, int64_t nnz, cudaStream_t s,
                     int64_t** d_toff, int32_t** d_tadj);

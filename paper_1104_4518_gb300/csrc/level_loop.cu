@@ -93,6 +93,7 @@ struct LoopParams {
   uint32_t* bits[3];
   uint32_t* vis;
   int64_t* chunks[2];
+  long long chunk_cap;  // entries of each chunk list
   LevelCtr* ctr;
   bfsdev::GridBarrier* bar;
   int* status;
@@ -142,6 +143,7 @@ __device__ __forceinline__ void claim_topdown(const LoopParams& p, int knext, in
 // Top-down visit of edge (u -> w) in phase k.
 __device__ __forceinline__ void td_visit(const LoopParams& p, const uint32_t* cur, uint32_t* nxt, int k,
                                          int u, int w, Acc& acc, Claims& cl) {
+  if (!bfsdev::in_range(p.status, bfsdev::kSiteTopDown, w, p.n)) return;
   const int ww = w >> 5;
   const uint32_t m = 1u << (w & 31);
   const uint32_t vw = p.vis[ww], cw = cur[ww], nw = nxt[ww];  // independent loads, one round trip
@@ -161,7 +163,8 @@ __device__ __forceinline__ void td_visit(const LoopParams& p, const uint32_t* cu
 // examined by lane g % 32 in sub-step g / 32, so every lane has kCoopSteps
 // adjacency loads and bitmap loads in flight.  A row whose slots hold a hit
 // takes the hit in its lowest slot (its highest position, i.e. its largest
-// id) and closes.  All lanes call it; returns the row's hit or -1.
+// id) and closes.  All lanes call it; returns the row's hit or -1.  status and
+// n serve the bounds-checking build's check of every id the scan loads.
 #ifndef BFS_COOP_STEPS
 #define BFS_COOP_STEPS 1
 #endif
@@ -169,7 +172,7 @@ constexpr int kCoopSteps = BFS_COOP_STEPS;
 constexpr int kCoopRow = 32 * kCoopSteps;
 
 __device__ __forceinline__ int scan_desc_coop(const int32_t* __restrict__ adj, const uint32_t* bm, long long b,
-                                              long long t, bool open, int hit, int lane) {
+                                              long long t, bool open, int hit, int lane, int* status, int n) {
   unsigned pm = __ballot_sync(kFull, open);
   while (pm) {
     const int rc = open ? (int)min(t - b, (long long)kCoopRow) : 0;
@@ -199,8 +202,12 @@ __device__ __forceinline__ int scan_desc_coop(const int32_t* __restrict__ adj, c
       u[sstep] = slot < total ? __ldg(&adj[tr - 1 - (slot - er)]) : -1;
     }
 #pragma unroll
-    for (int sstep = 0; sstep < kCoopSteps; ++sstep)
-      h[sstep] = u[sstep] >= 0 && ((bm[u[sstep] >> 5] >> (u[sstep] & 31)) & 1u);
+    for (int sstep = 0; sstep < kCoopSteps; ++sstep) {
+      const bool live = bfsdev::kBoundsCheck
+                            ? sstep * 32 + lane < total && bfsdev::in_range(status, bfsdev::kSitePull, u[sstep], n)
+                            : u[sstep] >= 0;
+      h[sstep] = live && ((bm[u[sstep] >> 5] >> (u[sstep] & 31)) & 1u);
+    }
     // this lane's row takes slots [excl, excl + cons) of the kCoopRow slots
     const int cons = max(0, min(rc, kCoopRow - excl));
     int found = -1;
@@ -456,8 +463,8 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      x0[q] = q < P0 ? cur[u0[q] >> 5] : 0u;
-      x1[q] = q < P1 ? cur[u1[q] >> 5] : 0u;
+      x0[q] = q < P0 && bfsdev::in_range(p.status, bfsdev::kSitePull, u0[q], p.n) ? cur[u0[q] >> 5] : 0u;
+      x1[q] = q < P1 && bfsdev::in_range(p.status, bfsdev::kSitePull, u1[q], p.n) ? cur[u1[q] >> 5] : 0u;
     }
     int h0 = -1, h1 = -1;
 #pragma unroll
@@ -466,8 +473,8 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
       if (q < P1 && h1 < 0 && ((x1[q] >> (u1[q] & 31)) & 1u)) h1 = u1[q];
     }
     const long long t0 = e0 - P0, t1 = e1 - P1;
-    h0 = scan_desc_coop(p.tadj, cur, b0, t0, a0 && h0 < 0 && t0 > b0, h0, lane);
-    h1 = scan_desc_coop(p.tadj, cur, b1, t1, a1 && h1 < 0 && t1 > b1, h1, lane);
+    h0 = scan_desc_coop(p.tadj, cur, b0, t0, a0 && h0 < 0 && t0 > b0, h0, lane, p.status, p.n);
+    h1 = scan_desc_coop(p.tadj, cur, b1, t1, a1 && h1 < 0 && t1 > b1, h1, lane, p.status, p.n);
     if (live0) pull_finish(p, nxt, w0, vw0, visw0, v0, h0, b0, e0, knext, acc, sm.cl, wq, nbuf, lane);
     if (live1) pull_finish(p, nxt, w1, vw1, visw1, v1, h1, b1, e1, knext, acc, sm.cl, wq, nbuf, lane);
   }
@@ -776,6 +783,7 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   p.vis = w->vis;
   p.chunks[0] = w->chunks[0];
   p.chunks[1] = w->chunks[1];
+  p.chunk_cap = w->chunk_cap;
   p.ctr = w->ctr;
   p.status = w->status;
   p.stats = w->stats;

@@ -27,7 +27,7 @@ constexpr int64_t kChunkCap = 2 * (kStaticMaxEntries / kChunkEdges) + kMaxSource
 constexpr size_t kChunkBytes = round256(sizeof(int64_t) * kChunkCap);
 constexpr size_t kCtrBytes = round256(sizeof(LevelCtr) * kCtrRing);
 constexpr size_t kBarrierBytes = round256(sizeof(bfsdev::GridBarrier));
-constexpr size_t kSmallBytes = 256;  // status, misc, edge count
+constexpr size_t kSmallBytes = 256;  // status (int[4]), misc, edge count, offset-check flag
 
 constexpr size_t kOffQueue = 0;
 constexpr size_t kOffBits = kOffQueue + 3 * kQueueBytes;
@@ -80,6 +80,11 @@ extern "C" int bfs_run_static(const int64_t* offsets, const int32_t* adj, int32_
   unsigned char* base = nullptr;
   if (int e = scratch_address(&base)) return e;
   cudaStream_t s = (cudaStream_t)stream;
+  if (bfsdev::kBoundsCheck) {  // the caller's rows must lie inside [0, nnz) before the kernel trusts them
+    int ok = 0;
+    if (int e = check_offsets(offsets, n, nnz, reinterpret_cast<int*>(base + kOffSmall + 192), s, &ok)) return e;
+    if (!ok) return fail(BFS_ERR_BOUNDS, "bfs_run_static: row offsets are not non-decreasing from 0 to nnz");
+  }
 
   // A graph and a workspace that only point at caller memory and at the scratch.
   bfs_graph g;
@@ -117,11 +122,11 @@ extern "C" int bfs_run_static(const int64_t* offsets, const int32_t* adj, int32_
   r.parent = parent_out;
   if (int e = launch_level_loop(r, s)) return e;
   BFS_CUDA_TRY(cudaStreamSynchronize(s));
-  int st = 0;
-  BFS_CUDA_TRY(cudaMemcpy(&st, w.status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (st != 0) {
+  int st[4] = {0, 0, 0, 0};
+  BFS_CUDA_TRY(cudaMemcpy(st, w.status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[0] != 0) {
     BFS_CUDA_TRY(cudaMemset(base + kOffBarrier, 0, kBarrierBytes + kSmallBytes));
-    return fail(st, "bfs_run_static: a device-side wait reached its limit; the traversal was abandoned");
+    return fail(st[0], "bfs_run_static: " + device_status_message(st));
   }
   return BFS_OK;
 }

@@ -1,7 +1,8 @@
 """CPU checks of the C-ABI library and of the oracle's independence (no GPU needed).
 
-- every function declared in include/bfs.h is exported by libbfs_gb300.so, and
-  nothing else is;
+- every function declared in include/bfs.h is exported by libbfs_gb300.so and
+  by its bounds-checking build libbfs_gb300_checked.so, and nothing else is;
+  each library says which build it is;
 - the product package never imports the oracle, and the oracle never includes
   or loads the library's sources.
 """
@@ -28,6 +29,12 @@ def libpath():
     return b.build()
 
 
+@pytest.fixture(scope="module")
+def checked_libpath():
+    from paper_1104_4518_gb300 import build as b
+    return b.build_checked()
+
+
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("bfs_graph_create", "bfs_graph_create_from_edges", "bfs_run", "bfs_run_batch",
@@ -45,6 +52,25 @@ def test_library_loads_and_exports_every_declared_symbol(libpath):
     assert exported == set(declared_functions())
     lib.bfs_version.restype = ctypes.c_char_p
     assert b"sm_103a" in lib.bfs_version()
+    assert lib.bfs_bounds_checked() == 0
+
+
+def test_bounds_checking_build_exports_the_same_symbols(checked_libpath):
+    lib = ctypes.CDLL(checked_libpath)
+    out = subprocess.run(["nm", "-D", "--defined-only", checked_libpath], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert exported == set(declared_functions())
+    assert lib.bfs_bounds_checked() == 1
+    lib.bfs_version.restype = ctypes.c_char_p
+    assert b"bounds-checking" in lib.bfs_version()
+
+
+def test_environment_selects_the_bounds_checking_library():
+    code = "import paper_1104_4518_gb300 as b; print(b.BOUNDS_CHECKED, b.LIB_PATH)"
+    for val, want in (("1", "libbfs_gb300_checked.so"), ("0", "libbfs_gb300.so")):
+        env = dict(os.environ, BFS_BOUNDS_CHECK=val)
+        out = subprocess.run(["python", "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, check=True)
+        assert out.stdout.split()[0] == str(val == "1") and out.stdout.split()[1].endswith(want)
 
 
 def test_version_and_error_string_need_no_gpu(libpath):
