@@ -10,6 +10,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "nvtx_range.h"
 
 namespace bfsint {
 
@@ -286,6 +287,7 @@ int bfs_bounds_checked(void) { return bfsdev::kBoundsCheck ? 1 : 0; }
 
 int bfs_graph_create(const int64_t* offsets, const int32_t* adj, int32_t n, int64_t nnz, uint32_t flags,
                      bfs_graph** out) {
+  NvtxRange nvtx_range("bfs_graph_create");
   if (!out) return fail(BFS_ERR_INVALID_ARG, "bfs_graph_create: NULL out");
   *out = nullptr;
   if (n < 1 || n >= 2147483647) return fail(BFS_ERR_INVALID_ARG, "bfs_graph_create: n out of range");
@@ -343,6 +345,7 @@ int bfs_graph_create(const int64_t* offsets, const int32_t* adj, int32_t n, int6
 
 int bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, uint32_t flags,
                                 void* stream, bfs_graph** out) {
+  NvtxRange nvtx_range("bfs_graph_create_from_edges");
   if (!out) return fail(BFS_ERR_INVALID_ARG, "bfs_graph_create_from_edges: NULL out");
   *out = nullptr;
   if (n < 1 || n >= 2147483647) return fail(BFS_ERR_INVALID_ARG, "bfs_graph_create_from_edges: n out of range");
@@ -393,6 +396,7 @@ int bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, int64_t 
 }
 
 int bfs_graph_union(bfs_graph* const* graphs, int32_t count, void* stream, bfs_graph** out) {
+  NvtxRange nvtx_range("bfs_graph_union");
   if (!out || !graphs || count < 1) return fail(BFS_ERR_INVALID_ARG, "bfs_graph_union: bad argument");
   *out = nullptr;
   std::vector<int64_t> base(count + 1, 0);
@@ -541,6 +545,7 @@ static int finish_run(Workspace* w, const bfs_opts* opts, cudaStream_t s, int mi
 
 int bfs_run(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_out, const bfs_opts* opts,
             void* stream) {
+  NvtxRange nvtx_range("bfs_run");
   if (int e = check_graph(g)) return e;
   if (source < 0 || source >= g->n) return fail(BFS_ERR_INVALID_ARG, "bfs_run: source outside [0, n)");
   if (!parent_out || !level_out) return fail(BFS_ERR_INVALID_ARG, "bfs_run: NULL output");
@@ -574,6 +579,7 @@ int bfs_run(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_ou
 
 int bfs_run_batch(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* parent_out, int32_t* level_out,
                   const bfs_opts* opts, void* stream) {
+  NvtxRange nvtx_range("bfs_run_batch");
   if (int e = check_graph(g)) return e;
   if (!sources || k < 1) return fail(BFS_ERR_INVALID_ARG, "bfs_run_batch: need k >= 1 sources");
   if (!parent_out || !level_out) return fail(BFS_ERR_INVALID_ARG, "bfs_run_batch: NULL output");
@@ -634,6 +640,7 @@ int bfs_run_batch(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* pare
 
 int bfs_run_ragged(bfs_graph* u, const int32_t* sources, int32_t* const* parent_out, int32_t* const* level_out,
                    const bfs_opts* opts, void* stream) {
+  NvtxRange nvtx_range("bfs_run_ragged");
   if (int e = check_graph(u)) return e;
   if (!sources || !parent_out || !level_out) return fail(BFS_ERR_INVALID_ARG, "bfs_run_ragged: NULL argument");
   const int parts = u->parts;
@@ -674,6 +681,7 @@ int bfs_run_ragged(bfs_graph* u, const int32_t* sources, int32_t* const* parent_
 }
 
 int bfs_sync(bfs_graph* g, void* stream) {
+  NvtxRange nvtx_range("bfs_sync");
   if (int e = check_graph(g)) return e;
   cudaStream_t s = (cudaStream_t)stream;
   Workspace* w = nullptr;
@@ -705,6 +713,7 @@ int bfs_get_tuning(const bfs_graph* g, bfs_tuning* t) {
 
 int bfs_selector_collect(bfs_graph* g, const int32_t* roots, int32_t nroots, int32_t reps, float* X, float* T,
                          int32_t max_rows, int32_t* rows_out, void* stream) {
+  NvtxRange nvtx_range("bfs_selector_collect");
   if (int e = check_graph(g)) return e;
   if (!roots || nroots < 1 || reps < 1 || !X || !T || max_rows < 0 || !rows_out)
     return fail(BFS_ERR_INVALID_ARG, "bfs_selector_collect: bad argument");
@@ -765,6 +774,7 @@ int bfs_selector_collect(bfs_graph* g, const int32_t* roots, int32_t nroots, int
 }
 
 int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning* best, void* stream) {
+  NvtxRange nvtx_range("bfs_autotune");
   if (int e = check_graph(g)) return e;
   if (!roots || nroots < 1) return fail(BFS_ERR_INVALID_ARG, "bfs_autotune: need roots");
   for (int i = 0; i < nroots; ++i)

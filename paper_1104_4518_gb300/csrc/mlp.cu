@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "nvtx_range.h"
 #include "mlp_device.cuh"
 
 namespace bfsint {
@@ -266,6 +267,7 @@ int bfs_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t t
 
 int bfs_selector_train(float* params, const float* X, const float* T, int32_t B, int32_t steps, float lr,
                        float* loss_history, void* stream) {
+  NvtxRange nvtx_range("bfs_selector_train");
   if (!params || !X || !T || B < 1 || steps < 0) return fail(BFS_ERR_INVALID_ARG, "bfs_selector_train: bad argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int ntiles = (B + kTS - 1) / kTS;

@@ -13,6 +13,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "nvtx_range.h"
 
 namespace bfsint {
 namespace {
@@ -70,6 +71,7 @@ using namespace bfsint;
 
 extern "C" int bfs_run_static(const int64_t* offsets, const int32_t* adj, int32_t n, int64_t nnz, int32_t source,
                               int32_t* parent_out, int32_t* level_out, void* stream) {
+  NvtxRange nvtx_range("bfs_run_static");
   if (n < 1 || n > kStaticMaxVertices)
     return fail(BFS_ERR_INVALID_ARG, "bfs_run_static: n must be in [1, 1048576] (size of the static scratch)");
   if (nnz < 0 || nnz > kStaticMaxEntries)
