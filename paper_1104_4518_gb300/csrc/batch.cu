@@ -358,9 +358,11 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
     const bool topdown = (long long)count <= p.td_limit;
     const int wid = tid >> 5;
     if (topdown) {
-      // frontier rows above kChunkEdges: one CTA per chunk item
+      // frontier rows above kChunkEdges: one CTA per chunk item, with room in the
+      // CTA's buffers for the item's claims
       const int64_t* items = p.chunks[k & 1];
       for (long long ci = blockIdx.x; ci < nchunks; ci += G) {
+        flush_claims_if_full(p, knext, cl, kChunkEdges, kBigBuf / 2);
         const int64_t it = items[ci];
         const int u = (int)(it >> 32);
         const long long rb = __ldg(&p.off[u]) + (it & 0xffffffffll) * kChunkEdges;

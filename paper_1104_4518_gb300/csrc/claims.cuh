@@ -192,4 +192,20 @@ __device__ __forceinline__ void flush_claims(const P& p, int knext, Claims& cl) 
   if (threadIdx.x == 0) claims_reset(cl);
 }
 
+// Flushes the CTA's buffers when fewer than qroom queue entries or bigroom
+// chunk requests are left, so that the work that follows cannot overflow them.
+// A claim that overflows the buffer costs a global atomic on the level's one
+// queue counter, and at scale 26 a top-down level that claims 2.9 M vertices
+// sent a million of those to one L2 slice, which the parent atomics of the
+// same level also use: the level took 0.81 ms instead of 0.44 ms.  Called by
+// every thread of the CTA at a point where the whole CTA is converged.
+template <typename P>
+__device__ __forceinline__ void flush_claims_if_full(const P& p, int knext, Claims& cl, int qroom, int bigroom) {
+  __syncthreads();
+  if (cl.qn > kQBuf - qroom || cl.nbig > kBigBuf - bigroom) {  // the same on every thread after the barrier
+    flush_claims(p, knext, cl);
+    __syncthreads();  // thread 0's reset of the counts lands before any thread claims again
+  }
+}
+
 }  // namespace bfsint

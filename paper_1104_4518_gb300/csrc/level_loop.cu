@@ -295,9 +295,11 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
   const int32_t* Q = p.queue[k % 3];
   const int tid = threadIdx.x, lane = tid & 31;
 
-  // chunk items of high-degree frontier vertices: one CTA per item
+  // chunk items of high-degree frontier vertices: one CTA per item; before each
+  // item the CTA makes room in its buffers for the item's claims
   const int64_t* items = p.chunks[k & 1];
   for (unsigned ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+    flush_claims_if_full(p, k + 1, sm.cl, kChunkEdges, kBigBuf / 2);
     const int64_t it = items[ci];
     const int v = (int)(it >> 32);
     const long long c = it & 0xffffffffll;
@@ -329,6 +331,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
     }
   } else {  // BFS_VARIANT_TD_BINNED
     for (long long tile = 0; tile < count; tile += gthreads) {
+      flush_claims_if_full(p, k + 1, sm.cl, kQBuf / 2, kBigBuf / 2);
       const long long i = tile + blockIdx.x + (long long)tid * G;
       int u = -1;
       long long b = 0, e = 0;
