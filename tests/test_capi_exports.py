@@ -10,6 +10,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -74,9 +75,13 @@ def test_environment_selects_the_bounds_checking_library():
 
 
 def test_version_and_error_string_need_no_gpu(libpath):
+    # a process that made no failing call has an empty message
+    code = ("import ctypes, sys; l = ctypes.CDLL(sys.argv[1]); l.bfs_last_error.restype = ctypes.c_char_p; "
+            "print(repr(l.bfs_last_error()))")
+    fresh = subprocess.run([sys.executable, "-c", code, libpath], capture_output=True, text=True, check=True)
+    assert fresh.stdout.strip() == "b''"
     lib = ctypes.CDLL(libpath)
     lib.bfs_last_error.restype = ctypes.c_char_p
-    assert lib.bfs_last_error() == b""
     # an argument error is reported without touching a device
     lib.bfs_graph_info.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     assert lib.bfs_graph_info(None, None, None, None) == 1
