@@ -55,3 +55,17 @@ def test_profile_traffic_counts_only_for_the_recorded_kernel_source(monkeypatch)
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.profile_traffic(name) is None
     assert bench.profile_traffic("no_such_profile.md") is None
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched like the multi-GPU bench (torchrun, 2 ranks): rank 0 alone times the
+    oracle and prints; the other rank exits 0 without work."""
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", "29517", os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--workload", "rmat16", "--steps", "1", "--warmup", "3", "--gpus", "2"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
