@@ -1,14 +1,15 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 BFS library: GTEPS on the paper-shaped synthetic workloads.
 
-Default workload (no flags): R-MAT scale 22, edgefactor 16, (A,B,C,D) =
+Default workload (no flags): R-MAT scale 26, edgefactor 16, (A,B,C,D) =
 (.57,.19,.19,.05), seeded relabelling, 64 seeded roots of degree >= 1 (graph seed
-2, root seed 102); one step = one single-root traversal (bfs_run, heuristic
-selector) from each of the 64 roots.  TEPS follows Sec. 6 of the paper: the
-edges counted for a root are the undirected edges of its component, and only
-roots in the large component enter the mean (the harmonic mean of per-root
-GTEPS).  Inputs (CSR adjacency, 0.5 GB) are larger than the 129 MB L2, so no
-flush is done between roots.
+3, root seed 103): the largest plain single-root configuration that fits one
+GPU.  One step = one single-root traversal (bfs_run, heuristic selector) from
+each of the 64 roots.  TEPS follows Sec. 6 of the paper: the edges counted for
+a root are the undirected edges of its component, and only roots in the large
+component enter the mean (the harmonic mean of per-root GTEPS).  Inputs (CSR
+adjacency, 8.6 GB) are far larger than the 129 MB L2, so no flush is done
+between roots.
 
 Printed (rank 0): one JSON line with value, roofline of the level-loop kernel,
 the oracle CPU baseline, the end-to-end figure (host outputs), clocks sampled
@@ -159,8 +160,11 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profile_traffic(name: str):
-    """Per-launch DRAM traffic from a committed ncu summary, if it matches the current kernel source."""
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal
+
+
+def profile_summary(name: str):
+    """The `- key: value` lines of a committed ncu summary under profiles/, or None."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         text = open(path).read()
@@ -171,12 +175,44 @@ def profile_traffic(name: str):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
-    if kv.get("source_sha256") != kernel_source_hash():
+    return kv
+
+
+def profile_traffic(name: str):
+    """Per-launch DRAM traffic from a committed ncu summary, if it matches the current kernel source."""
+    kv = profile_summary(name)
+    if kv is None or kv.get("source_sha256") != kernel_source_hash():
         return None
     try:
         return float(kv["traffic_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+# ncu captures stay on small cases; larger R-MAT workloads scale this one.
+SCALED_CAPTURE = "level_loop_rmat23.md"
+
+
+def traffic_estimate(workload: str, algo_bytes: float):
+    """(DRAM bytes per level-loop launch, how it was obtained) for `workload`.
+
+    A capture of the same workload counts as it is.  Otherwise an R-MAT
+    workload takes the scale-23 capture scaled by the ratio of algorithmic bytes
+    per launch: a traversal's traffic grows with the rows, offsets and outputs
+    it touches, which is what the algorithmic bytes count.  Captures whose
+    kernel source hash differs from the current source count as missing."""
+    own = profile_traffic(f"level_loop_{workload}.md")
+    if own is not None:
+        return own, f"ncu capture of this workload (profiles/level_loop_{workload}.md)"
+    kv = profile_summary(SCALED_CAPTURE)
+    if workload.startswith("rmat") and kv is not None and kv.get("source_sha256") == kernel_source_hash():
+        try:
+            t, a = float(kv["traffic_bytes_per_launch"]), float(kv["algorithmic_bytes_per_launch"])
+        except (KeyError, ValueError):
+            return None, "scaled capture lacks its byte counts"
+        return t * algo_bytes / a, (f"profiles/{SCALED_CAPTURE} (R-MAT scale 23, one launch) scaled by the "
+                                    f"ratio of algorithmic bytes per launch, {algo_bytes / a:.3f}")
+    return None, "no ncu capture of the current kernel source"
 
 
 def kernel_source_hash() -> str:
@@ -194,31 +230,127 @@ def harmonic_gteps(edges, times_s):
     return len(rates) / sum(1.0 / r for r in rates) if rates else 0.0
 
 
-def cpu_oracle_sample(el, roots_large, max_threads=16, budget_s=20.0):
-    """Times the oracle BFS (serial per root) on up to `max_threads` roots at once."""
+def bench_config(wl: dict, n: int, nnz: int, roots: int, n_large: int, teps_edges: int, world: int) -> dict:
+    """The `config` object of the JSON line; both arms print the same one."""
+    return {"workload": workload_name(wl), "n": int(n), "nnz": int(nnz), "roots": int(roots),
+            "roots_in_large_component": int(n_large), "teps_edges_per_root": int(teps_edges),
+            "selector": "heuristic", "l2": "not flushed: the CSR adjacency is larger than the 129 MB L2",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def oracle_census(og, roots):
+    """(roots in the large component, that component's TEPS edges), found by the oracle.
+
+    A BFS from the first root (of the first four) whose component holds more than 2/3 of the
+    graph's edges settles it: every other component then has fewer than half
+    as many edges, so the large-component rule (at least half the largest
+    root component's edges) keeps exactly the roots that BFS reached.  If no
+    root's component is that large, every root is traversed."""
+    import oracle
+
+    total = og.nnz // 2
+    for s in roots[:4]:
+        lv, _, _ = oracle.bfs(og, int(s))
+        e = oracle.component_edges(og, lv)
+        if 3 * e > 2 * total:
+            return [int(r) for r in roots if lv[int(r)] >= 0], e
+    res = oracle.bfs_many(og, [int(r) for r in roots])
+    edges = [oracle.component_edges(og, lv) for lv, _, _ in res]
+    emax = max(edges)
+    large = [int(r) for r, e in zip(roots, edges) if e >= 0.5 * emax]
+    return large, emax
+
+
+def host_threads() -> int:
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def timed_oracle_steps(og, step_roots, threads):
+    """Wall time of one serial oracle BFS per entry of step_roots, `threads` at a time."""
     from concurrent.futures import ThreadPoolExecutor
 
     import oracle
 
-    og = oracle.csr_of(el)
-    cores = os.cpu_count() or 1
-    threads = max(1, min(max_threads, cores, len(roots_large)))
-    sample = [int(r) for r in roots_large[:threads]]
-
-    def one(s):
-        t0 = time.perf_counter()
-        level, _, _ = oracle.bfs(og, s)
-        t = time.perf_counter() - t0
-        return t, oracle.component_edges(og, level)
-
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
-        res = list(ex.map(one, sample))
-    wall = time.perf_counter() - t0
-    edges = [e for _, e in res]
-    return {"wall_s": wall, "edges": edges, "times": [t for t, _ in res], "threads": threads,
-            "sample": f"{len(sample)} large-component roots of the same graph, one oracle BFS per thread "
-                      f"(serial FIFO BFS + max-id parent pass), oracle CSR build not timed"}
+        list(ex.map(lambda s: oracle.bfs(og, s), step_roots))
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_sample(el, roots_large, teps_edges):
+    """The oracle (serial FIFO BFS + max-id parent pass) on the host cores: one
+    large-component root per thread, all threads at once."""
+    import oracle
+
+    og = oracle.csr_of(el)
+    threads = max(1, min(host_threads(), len(roots_large)))
+    sample = [int(r) for r in roots_large[:threads]]
+    wall = timed_oracle_steps(og, sample, threads)
+    return {"value": teps_edges * len(sample) / wall / 1e9, "threads": threads,
+            "sample": f"{len(sample)} large-component roots of the same graph, one serial oracle BFS per "
+                      f"thread on {threads} threads at once ({wall:.1f} s wall); oracle CSR build not timed"}
+
+
+def event_pair():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def timed_roots(run_one, roots, steps, warmup, stream):
+    """Per-root device times (ms, [steps][roots]) of run_one(root) after `warmup` untimed passes."""
+    import torch
+
+    for _ in range(warmup):
+        for s in roots:
+            run_one(int(s))
+    torch.cuda.synchronize()
+    ev = [[event_pair() for _ in roots] for _ in range(steps)]
+    for k in range(steps):
+        for i, s in enumerate(roots):
+            ev[k][i][0].record(stream)
+            run_one(int(s))
+            ev[k][i][1].record(stream)
+    torch.cuda.synchronize()
+    return np.array([[a.elapsed_time(b) for a, b in row] for row in ev])
+
+
+def batched_config_comparison(bfs, stream):
+    """Batched against plain on R-MAT scale 24 (the batched configuration): GTEPS of one
+    64-root batched traversal and of the 64 single-root traversals of the same roots."""
+    import torch
+
+    wl = WORKLOADS["rmat24"]
+    el, roots = make_workload(wl)
+    g = bfs.bfs_graph_create_from_edges(torch.from_numpy(el.src).cuda(), torch.from_numpy(el.dst).cuda(), el.n)
+    del el
+    n, _, _ = g.info()
+    rl = [int(s) for s in roots]
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    edges = []
+    for s in rl:
+        o = bfs.RunOptions(want_counts=True)
+        bfs.bfs_run(g, s, parent, level, o)
+        edges.append(o.edges)
+    pt = timed_roots(lambda s: bfs.bfs_run(g, s, parent, level), rl, 3, 3, stream)
+    plain_ms = float(pt.sum(axis=1).mean())
+    pb = torch.empty((len(rl), n), dtype=torch.int32, device="cuda")
+    lb = torch.empty((len(rl), n), dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        bfs.bfs_run_batch(g, rl, pb, lb)
+    e0, e1 = event_pair()
+    e0.record(stream)
+    for _ in range(3):
+        bfs.bfs_run_batch(g, rl, pb, lb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1) / 3
+    g.destroy()
+    return {"workload": workload_name(wl), "batched_ms_per_64_roots": round(bms, 3),
+            "plain_ms_per_64_roots": round(plain_ms, 3),
+            "batched_gteps": round(sum(edges) / (bms / 1e3) / 1e9, 3),
+            "plain_gteps": round(sum(edges) / (plain_ms / 1e3) / 1e9, 3)}
 
 
 # ---------------- the GPU arm ----------------
@@ -259,15 +391,13 @@ def run_gpu(args, wl):
     bfs.bfs_sync(g)
 
     R = len(roots)
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(R)]
-          for _ in range(args.steps)]
+    ev = [[event_pair() for _ in range(R)] for _ in range(args.steps)]
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
+    t_start, t_end = event_pair()
     t_start.record(stream)
     for k in range(args.steps):
         for i, s in enumerate(roots):
@@ -293,22 +423,26 @@ def run_gpu(args, wl):
     algo_bytes = float(np.mean(comp_bytes))
     mean_launch_s = float(root_ms.mean()) / 1e3
     achieved = algo_bytes / mean_launch_s / 1e9
-    traffic = profile_traffic(f"level_loop_{args.workload}.md")
+    traffic, traffic_how = traffic_estimate(args.workload, algo_bytes)
+    roof = {"bound": "hbm", "kernel": "level_loop_kernel", "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "peak_kind": f"{peak_kind} (copy bandwidth, burst: each launch timed alone)",
+            "frac_of_nominal_8tbs": round(achieved / NOMINAL_HBM_GBS, 4),
+            "algorithmic_bytes_per_launch": round(algo_bytes),
+            "bytes_model": "4*sum deg(reached) + 16*n_reached + 8*n per root",
+            "traffic": round(traffic) if traffic is not None else None, "traffic_source": traffic_how}
+    if traffic is not None:
+        dram = traffic / mean_launch_s / 1e9
+        roof["dram_achieved"] = round(dram, 1)
+        roof["dram_frac"] = round(dram / peak, 4)
+        roof["traffic_over_algorithmic"] = round(traffic / algo_bytes, 3)
 
+    cfg = bench_config(wl, n, nnz, R, len(large), edges[large[0]], world)
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded generators)",
-        "config": {"workload": workload_name(wl), "n": n, "nnz": nnz, "roots": R, "roots_in_large_component": len(large),
-                   "teps_edges_per_root": int(edges[large[0]]), "selector": "heuristic",
-                   "l2": "not flushed: the CSR adjacency is larger than the 129 MB L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "level_loop_kernel", "achieved": round(achieved, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "peak_kind": f"{peak_kind} (copy bandwidth, burst: each launch timed alone)",
-                     "algorithmic_bytes_per_launch": round(algo_bytes),
-                     "traffic": traffic,
-                     "bytes_model": "4*sum deg(reached) + 16*n_reached + 8*n per root"},
+        "config": cfg, "roofline": roof,
         "gpu_launches": args.steps * R * world,  # one level-loop launch per root, every rank
         "clocks": clk,
         "aggregate_gteps": round(agg_edges / agg_time / 1e9, 3),
@@ -342,69 +476,72 @@ def run_gpu(args, wl):
                          "how": "bfs_run with BFS_HOST_PTRS into pinned host buffers; the library copies "
                                 "parent and level back and synchronises; host wall clock per root"}
 
-    # side comparisons (rank 0, once): batched and learned selector on the same roots
+    # side comparisons (rank 0, once): batched, autotuned, learned selector and
+    # every single variant forced at every level, on the same graph and roots
     if rank == 0 and not args.no_compare:
         comp = {}
+        large_roots = [int(roots[i]) for i in large]
+        e_one = [edges[i] for i in large]
         k = min(64, R)
         pb = torch.empty((k, n), dtype=torch.int32, device="cuda")
         lb = torch.empty((k, n), dtype=torch.int32, device="cuda")
         for _ in range(2):
             bfs.bfs_run_batch(g, [int(s) for s in roots[:k]], pb, lb)
         bfs.bfs_sync(g)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = event_pair()
         reps = 3
         e0.record()
         for _ in range(reps):
             bfs.bfs_run_batch(g, [int(s) for s in roots[:k]], pb, lb)
         e1.record()
         torch.cuda.synchronize()
+        del pb, lb
         bms = e0.elapsed_time(e1) / reps
         comp["batched_gteps"] = round(sum(edges[:k]) / (bms / 1e3) / 1e9, 3)
         comp["batched_ms_per_64_roots"] = round(bms, 3)
         comp["plain_ms_per_64_roots"] = round(float(root_ms[:, :k].sum(axis=1).mean()), 3)
-        # autotuned: tuning picked on 8 other seeded roots, then all timed roots
-        if wl["kind"] == "rmat":
-            tune_roots = inputs.roots(el, 8, wl["root_seed"] + 7777)
-            tuned = bfs.bfs_autotune(g, tune_roots)
-            evt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in large]
-            for s in roots:
-                bfs.bfs_run(g, int(s), parent, level)
-            for (a, b), i in zip(evt, large):
-                a.record()
-                bfs.bfs_run(g, int(roots[i]), parent, level)
-                b.record()
-            torch.cuda.synchronize()
-            comp["autotuned_gteps"] = round(harmonic_gteps([edges[i] for i in large],
-                                                           [a.elapsed_time(b) / 1e3 for a, b in evt]), 3)
-            comp["autotuned"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuned.as_dict().items()}
-            bfs.bfs_set_tuning(g, **{f: 0 for f in ("warp_degree", "cta_degree", "pull_thread_degree",
-                                                     "chunk_degree", "batch_topdown_limit", "small_frontier",
-                                                     "batch_width")}, alpha=0.0, beta=0.0)
+        # learned selector: same roots, same steps and warm-up as the plain figure
         wpath = os.path.join(ROOT, "paper_1104_4518_gb300", "selector_weights.bin")
         if os.path.exists(wpath):
             bfs.bfs_selector_load(wpath)
             lo = bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED)
-            for s in roots:
-                bfs.bfs_run(g, int(s), parent, level, lo)
+            lt = timed_roots(lambda s: bfs.bfs_run(g, s, parent, level, lo), large_roots, args.steps,
+                             args.warmup, stream)
             bfs.bfs_sync(g)
-            evl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in large]
-            for (a, b), i in zip(evl, large):
-                a.record()
-                bfs.bfs_run(g, int(roots[i]), parent, level, lo)
-                b.record()
-            torch.cuda.synchronize()
-            lt = [a.elapsed_time(b) / 1e3 for a, b in evl]
-            comp["learned_gteps"] = round(harmonic_gteps([edges[i] for i in large], lt), 3)
+            comp["learned_gteps"] = round(harmonic_gteps(e_one * args.steps, list(lt.flatten() / 1e3)), 3)
             bfs.bfs_selector_set_params(None)
+        # one variant at every level (Sec. 5.2's comparison of expansion schemes): 4 roots each
+        few = large_roots[:4]
+        var = {}
+        for vi, name in enumerate(bfs.VARIANT_NAMES):
+            fo = bfs.RunOptions(selector=bfs.BFS_SELECT_FORCED, forced_variant=vi)
+            ft = timed_roots(lambda s: bfs.bfs_run(g, s, parent, level, fo), few, 1, 1, stream)
+            var[name] = round(harmonic_gteps(e_one[:len(few)], list(ft.flatten() / 1e3)), 3)
+        bfs.bfs_sync(g)
+        comp["forced_variant_gteps_4_roots"] = var
+        # autotuned: tuning picked on 8 other seeded roots, then all timed roots
+        if wl["kind"] == "rmat":
+            tune_roots = inputs.roots(el, 8, wl["root_seed"] + 7777)
+            tuned = bfs.bfs_autotune(g, tune_roots)
+            at = timed_roots(lambda s: bfs.bfs_run(g, s, parent, level), large_roots, 1, 1, stream)
+            comp["autotuned_gteps"] = round(harmonic_gteps(e_one, list(at.flatten() / 1e3)), 3)
+            comp["autotuned"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuned.as_dict().items()}
+            bfs.bfs_set_tuning(g, **{f: 0 for f in ("warp_degree", "cta_degree", "pull_thread_degree",
+                                                     "chunk_degree", "batch_topdown_limit", "small_frontier",
+                                                     "batch_width")}, alpha=0.0, beta=0.0)
+        # the batched configuration's own graph (R-MAT scale 24, graph seed 4 / roots 104): 64 roots in
+        # one batched traversal against 64 single-root traversals of the same roots
+        if wl["kind"] == "rmat" and wl["scale"] != 24 and not args.no_batched_config:
+            comp["batched_rmat24"] = batched_config_comparison(bfs, stream)
         result["comparisons"] = comp
 
+    g.destroy()
+    del parent, level
     # CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cs = cpu_oracle_sample(el, [roots[i] for i in large])
-        result["cpu_baseline"] = {"value": round(sum(cs["edges"]) / cs["wall_s"] / 1e9, 5), "unit": "GTEPS",
-                                  "cores": cs["threads"], "kind": "oracle", "sample": cs["sample"],
-                                  "per_core_gteps": round(harmonic_gteps(cs["edges"], cs["times"]), 5)}
-    g.destroy()
+        cs = cpu_oracle_sample(el, [roots[i] for i in large], edges[large[0]])
+        result["cpu_baseline"] = {"value": round(cs["value"], 5), "unit": "GTEPS", "cores": cs["threads"],
+                                  "host_cpus": os.cpu_count(), "kind": "oracle", "sample": cs["sample"]}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -414,6 +551,9 @@ def run_gpu(args, wl):
 # ---------------- the reference arm: the CPU oracle ----------------
 
 def run_reference(args, wl):
+    """The oracle timed on the host cores on the GPU arm's workload.  One step is
+    one serial oracle BFS from a large-component root (the roots taken in turn);
+    the W warm-up steps and then the K timed steps run `threads` at a time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -421,36 +561,24 @@ def run_reference(args, wl):
 
     el, roots = make_workload(wl, 0)
     og = oracle.csr_of(el)
-    # which roots are in the large component (by the oracle's own traversal)
-    first = oracle.bfs_many(og, roots)
-    edges = [oracle.component_edges(og, lv) for lv, _, _ in first]
-    emax = max(edges)
-    large = [int(roots[i]) for i, e in enumerate(edges) if e >= 0.5 * emax]
-    ecomp = emax
-    cores = os.cpu_count() or 1
-    threads = max(1, min(16, cores, len(large)))
-    sample = large[:threads]
-
-    def step():
-        from concurrent.futures import ThreadPoolExecutor
-        with ThreadPoolExecutor(max_workers=threads) as ex:
-            list(ex.map(lambda s: oracle.bfs(og, s), sample))
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    wall = time.perf_counter() - t0
-    value = ecomp * len(sample) * args.steps / wall / 1e9
+    del el
+    large, e_comp = oracle_census(og, roots)
+    threads = host_threads()
+    seq = [large[i % len(large)] for i in range(args.warmup + args.steps)]
+    timed_oracle_steps(og, seq[:args.warmup], threads)
+    wall = timed_oracle_steps(og, seq[args.warmup:], threads)
+    value = e_comp * args.steps / wall / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GTEPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded generators)",
-            "config": {"workload": workload_name(wl), "n": og.n, "nnz": og.nnz},
-            "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": threads, "kind": "oracle",
-                             "sample": f"each step: {len(sample)} large-component roots, one serial oracle BFS per "
-                                       f"thread on {threads} host threads; oracle CSR build not timed"},
+            "config": bench_config(wl, og.n, og.nnz, len(roots), len(large), e_comp, world),
+            "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": min(threads, args.steps),
+                             "host_cpus": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step: one serial oracle BFS (FIFO queue + max-id parent pass) from "
+                                       f"a large-component root, the roots taken in turn; the {args.steps} timed "
+                                       f"steps run {threads} at a time on the host threads; oracle CSR build "
+                                       f"not timed"},
             "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -461,10 +589,11 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat22")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat26")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched-config", action="store_true")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # the timing rules ask for at least three untimed steps
     wl = WORKLOADS[args.workload]

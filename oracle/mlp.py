@@ -93,6 +93,42 @@ def loss_and_grad(flat: np.ndarray, X: np.ndarray, T: np.ndarray):
     return mse_loss(Y, T), backward(flat, cache, dY)
 
 
+def grad_scale(flat: np.ndarray, X: np.ndarray, T: np.ndarray) -> np.ndarray:
+    """Magnitude scale of each gradient entry: the chain rule of `loss_and_grad`
+    evaluated on absolute values (weights, biases, inputs, hidden activations and
+    the output error |Y| + |T|) with the ReLU masks of the exact evaluation.
+
+    Every gradient entry is a sum of products; the rounding error of evaluating
+    such an expression in floating point is bounded by a small multiple of the
+    unit roundoff times the same expression with every operand replaced by its
+    absolute value (Higham, "Accuracy and Stability of Numerical Algorithms",
+    Ch. 3-4: |fl(sum x_i) - sum x_i| <= gamma_n sum |x_i|).  Where the terms
+    cancel, the plain relative error is unbounded, so float32 results are
+    compared with the float64 gradient relative to this scale.  It is never
+    below |gradient|, and equals it when no term has a negative sign.
+    """
+    p = unpack(np.asarray(flat, dtype=np.float64))
+    a = {k: np.abs(v) for k, v in p.items()}
+    X = np.asarray(X, dtype=np.float64)
+    Y, (_, z1, _, z2, _) = forward(flat, X)
+    m1, m2 = z1 > 0.0, z2 > 0.0
+    Xa = np.abs(X)
+    h1 = np.where(m1, Xa @ a["W1"] + a["b1"], 0.0)
+    h2 = np.where(m2, h1 @ a["W2"] + a["b2"], 0.0)
+    dY = 2.0 * (np.abs(Y) + np.abs(np.asarray(T, dtype=np.float64))) / Y.size
+    g = np.zeros(N_PARAMS, dtype=np.float64)
+    gp = unpack(g)
+    gp["W3"][...] = h2.T @ dY
+    gp["b3"][...] = dY.sum(axis=0)
+    dz2 = (dY @ a["W3"].T) * m2
+    gp["W2"][...] = h1.T @ dz2
+    gp["b2"][...] = dz2.sum(axis=0)
+    dz1 = (dz2 @ a["W2"].T) * m1
+    gp["W1"][...] = Xa.T @ dz1
+    gp["b1"][...] = dz1.sum(axis=0)
+    return g
+
+
 def adam_step(flat, grad, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update at step t >= 1; returns new (flat, m, v)."""
     m = beta1 * m + (1.0 - beta1) * grad

@@ -26,12 +26,13 @@
 //     kChunkEdges edges, one CTA each.
 //   pull: for every vertex v not yet reached, scan its sorted row from the
 //     largest id down; the first neighbour in f_k is the max-id parent.  One
-//     warp owns 32 consecutive vertices (one bitmap word), so nxt / vis words
-//     are written without atomics.  Each lane first probes the top entries of
-//     its own row; rows still open are then scanned by the whole warp, 32
-//     entries per step, packed across rows by a warp prefix sum (per-row early
-//     exit is kept).  Vertices without edges are marked visited at init, so
-//     pull levels never touch them.
+//     warp owns a chunk of 32 bitmap words (1,024 vertices) at a time, so nxt /
+//     vis words are written by their owner lane without atomics; the chunk's
+//     live rows are dealt to the lanes, two per lane.  Each lane first probes
+//     the top entries of its rows; rows still open are then scanned by the
+//     whole warp, 32 entries per step, packed across rows by a warp prefix sum
+//     (per-row early exit is kept).  Vertices without edges are marked visited
+//     at init, so pull levels never touch them.
 #include <cooperative_groups.h>
 #include <cooperative_groups/scan.h>
 
@@ -283,6 +284,7 @@ struct Smem {
   long long tb[kBlock];
   int tpref[kBlock + 1];
   Claims cl;
+  uint32_t pull_hits[kWarps][32];  // pull: hit bits of each warp's 32 bitmap words
   __align__(16) float h1[64];  // selector network: hidden layer 1, choice
   int choice;
 };
@@ -401,28 +403,110 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
 }
 
 // ---------------- pull phase ----------------
-// Finishes one bitmap word of the pull phase: bitmap words, outputs, counters, queue.
-__device__ __forceinline__ void pull_finish(const LoopParams& p, uint32_t* nxt, long long ww, uint32_t vw,
-                                            uint32_t visw, int v, int hit, long long b, long long e, int knext,
-                                            Acc& acc, Claims& cl, int* wq, int& nbuf, int lane) {
-  const unsigned hits = __ballot_sync(kFull, hit >= 0);
-  if (lane == 0) {
-    if (hits) nxt[ww] = hits;
-    if ((visw | hits) != vw) p.vis[ww] = visw | hits;
+// Position of the r-th (0-based) set bit of m; r < popc(m).
+__device__ __forceinline__ int select_bit(uint32_t m, int r) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const int c = __popc(m & ((1u << s) - 1u));  // set bits in the low s bits
+    if (r >= c) {
+      r -= c;
+      m >>= s;
+      pos += s;
+    }
   }
+  return pos;
+}
+
+// The idx-th live vertex of a warp's chunk of 32 bitmap words (all lanes call
+// it; lane l holds word l's live bits `live` and the inclusive prefix `incl` of
+// their counts).  Returns the vertex, the owner lane of its word and its bit.
+__device__ __forceinline__ int live_vertex(long long chunk, uint32_t live, int incl, int idx, int& owner,
+                                           uint32_t& bit) {
+  int o = 0;  // number of lanes whose inclusive prefix is <= idx: the owner
+#pragma unroll
+  for (int st = 16; st >= 1; st >>= 1) {
+    const int c = __shfl_sync(kFull, incl, o + st - 1);
+    if (c <= idx) o += st;
+  }
+  o = min(o, 31);
+  const uint32_t lo = __shfl_sync(kFull, live, o);
+  const int excl_o = __shfl_sync(kFull, incl, o) - __popc(lo);
+  const int b = select_bit(lo, max(idx - excl_o, 0));
+  owner = o;
+  bit = 1u << b;
+  return (int)((chunk * 32 + o) * 32 + b);
+}
+
+// The max-id frontier neighbour of one row per lane (v < 0: no row), for two
+// rows per lane at once: row bounds, a probe of the top `probe` entries of
+// each row with their frontier words in flight together, then the warp's
+// cooperative descending scan of the rows still open.
+__device__ __forceinline__ void pull_rows2(const LoopParams& p, const uint32_t* cur, int probe, int lane, int va,
+                                           int vb, int& ha, int& hb, long long& ea, long long& da, long long& eb,
+                                           long long& db) {
+  long long ba = 0, bb = 0;
+  ea = eb = 0;
+  if (va >= 0) {
+    ba = __ldg(&p.toff[va]);
+    ea = __ldg(&p.toff[va + 1]);
+  }
+  if (vb >= 0) {
+    bb = __ldg(&p.toff[vb]);
+    eb = __ldg(&p.toff[vb + 1]);
+  }
+  const int PA = va >= 0 ? (int)min((long long)probe, ea - ba) : 0;
+  const int PB = vb >= 0 ? (int)min((long long)probe, eb - bb) : 0;
+  int ua[4], ub[4];
+  uint32_t xa[4], xb[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ua[q] = q < PA ? __ldg(&p.tadj[ea - 1 - q]) : 0;
+    ub[q] = q < PB ? __ldg(&p.tadj[eb - 1 - q]) : 0;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    xa[q] = q < PA && bfsdev::in_range(p.status, bfsdev::kSitePull, ua[q], p.n) ? cur[ua[q] >> 5] : 0u;
+    xb[q] = q < PB && bfsdev::in_range(p.status, bfsdev::kSitePull, ub[q], p.n) ? cur[ub[q] >> 5] : 0u;
+  }
+  ha = hb = -1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q < PA && ha < 0 && ((xa[q] >> (ua[q] & 31)) & 1u)) ha = ua[q];
+    if (q < PB && hb < 0 && ((xb[q] >> (ub[q] & 31)) & 1u)) hb = ub[q];
+  }
+  const long long ta = ea - PA, tb = eb - PB;
+  ha = scan_desc_coop(p.tadj, cur, ba, ta, va >= 0 && ha < 0 && ta > ba, ha, lane, p.status, p.n);
+  hb = scan_desc_coop(p.tadj, cur, bb, tb, vb >= 0 && hb < 0 && tb > bb, hb, lane, p.status, p.n);
+  da = ea - ba;
+  db = eb - bb;
+}
+
+// Bookkeeping of a vertex v reached by the pull (hit = its parent): outputs,
+// counters, chunk items, the owner word's hit bit and the warp's queue buffer.
+__device__ __forceinline__ void pull_claim(const LoopParams& p, int knext, int v, int hit, long long deg_in,
+                                           uint32_t* hitw, int owner, uint32_t bit, Acc& acc, Claims& cl, int* wq,
+                                           int& nbuf, int lane) {
   if (hit >= 0) {
     p.parent[v] = hit;
     p.level[v] = knext;
+    atomicOr(&hitw[owner], bit);
     // out-degree: the next level expands v's out-row (the row scanned here when undirected)
-    const long long deg = p.directed ? __ldg(&p.off[v + 1]) - __ldg(&p.off[v]) : e - b;
+    const long long deg = p.directed ? __ldg(&p.off[v + 1]) - __ldg(&p.off[v]) : deg_in;
     acc_vertex(acc, deg);
     if (deg > p.chunk_deg) push_chunks_cta(p, knext, cl, v, deg);
   }
-  if (hits) warp_enqueue(p, knext, wq, nbuf, hit >= 0, v, lane, false);
+  warp_enqueue(p, knext, wq, nbuf, hit >= 0, v, lane, false);
 }
 
-// Two bitmap words per warp step: the offset, probe and bitmap loads of both
-// words are issued together, then each word's open rows get the warp scan.
+// Dense-frontier SpMV over the unvisited rows.  A warp takes a chunk of 32
+// bitmap words (1,024 vertices) at a time: lane l loads word l of `vis` and of
+// `cur`, and the chunk's live vertices (not reached, not edgeless) are dealt to
+// the lanes 64 at a time, two rows per lane, so that every lane carries an open
+// row however sparse the live vertices are (in the last pull levels of a
+// scale-26 R-MAT graph most words hold one live vertex).  Each word's hits are
+// gathered in shared memory and its owner lane writes the word's `nxt` and
+// `vis` (no global atomics on the bitmaps).
 __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
   const uint32_t* cur = p.bits[k % 3];
   uint32_t* nxt = p.bits[(k + 1) % 3];
@@ -431,55 +515,46 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
   const int knext = k + 1;
   const int probe = min(p.pull_thread_deg, 4);
   int* wq = sm.cl.wq[wid];
+  uint32_t* hitw = sm.pull_hits[wid];
   int nbuf = 0;
-  for (long long w0 = ((long long)blockIdx.x * kBlock + threadIdx.x) / 32; w0 < p.nwords; w0 += 2 * gwarps) {
-    const long long w1 = w0 + gwarps;
-    const bool has1 = w1 < p.nwords;
-    const uint32_t vw0 = p.vis[w0], cw0 = cur[w0];
-    const uint32_t vw1 = has1 ? p.vis[w1] : 0xffffffffu, cw1 = has1 ? cur[w1] : 0u;
-    const uint32_t visw0 = vw0 | cw0, visw1 = vw1 | cw1;
-    if (lane == 0) {
-      if (visw0 == 0xffffffffu && vw0 != visw0) p.vis[w0] = visw0;
-      if (has1 && visw1 == 0xffffffffu && vw1 != visw1) p.vis[w1] = visw1;
-    }
-    const bool live0 = visw0 != 0xffffffffu, live1 = visw1 != 0xffffffffu;
-    if (!live0 && !live1) continue;
-    const int v0 = (int)(w0 * 32 + lane), v1 = (int)(w1 * 32 + lane);
-    const bool a0 = live0 && !((visw0 >> lane) & 1u), a1 = live1 && !((visw1 >> lane) & 1u);
-    long long b0 = 0, e0 = 0, b1 = 0, e1 = 0;
-    if (a0) {
-      b0 = __ldg(&p.toff[v0]);
-      e0 = __ldg(&p.toff[v0 + 1]);
-    }
-    if (a1) {
-      b1 = __ldg(&p.toff[v1]);
-      e1 = __ldg(&p.toff[v1 + 1]);
-    }
-    const int P0 = a0 ? (int)min((long long)probe, e0 - b0) : 0;
-    const int P1 = a1 ? (int)min((long long)probe, e1 - b1) : 0;
-    int u0[4], u1[4];
-    uint32_t x0[4], x1[4];
+  const long long nchunks = ((long long)p.nwords + 31) / 32;
+  for (long long c = (long long)wid * gridDim.x + blockIdx.x; c < nchunks; c += gwarps) {
+    const long long w = c * 32 + lane;
+    const bool has = w < p.nwords;
+    const uint32_t vw = has ? p.vis[w] : 0xffffffffu;
+    const uint32_t cw = has ? cur[w] : 0u;
+    const uint32_t visw = vw | cw;
+    const uint32_t live = ~visw;
+    const int cnt = __popc(live);
+    int incl = cnt;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      u0[q] = q < P0 ? __ldg(&p.tadj[e0 - 1 - q]) : 0;
-      u1[q] = q < P1 ? __ldg(&p.tadj[e1 - 1 - q]) : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      x0[q] = q < P0 && bfsdev::in_range(p.status, bfsdev::kSitePull, u0[q], p.n) ? cur[u0[q] >> 5] : 0u;
-      x1[q] = q < P1 && bfsdev::in_range(p.status, bfsdev::kSitePull, u1[q], p.n) ? cur[u1[q] >> 5] : 0u;
+    const int total = __shfl_sync(kFull, incl, 31);
+    hitw[lane] = 0u;
+    __syncwarp();
+    for (int base = 0; base < total; base += 64) {
+      int oa, ob;
+      uint32_t bita, bitb;
+      const int ia = base + lane, ib = base + 32 + lane;
+      const int la = live_vertex(c, live, incl, min(ia, total - 1), oa, bita);
+      const int lb = live_vertex(c, live, incl, min(ib, total - 1), ob, bitb);
+      const int va = ia < total ? la : -1, vb = ib < total ? lb : -1;
+      int ha, hb;
+      long long ea, da, eb, db;
+      pull_rows2(p, cur, probe, lane, va, vb, ha, hb, ea, da, eb, db);
+      pull_claim(p, knext, va, va >= 0 ? ha : -1, da, hitw, oa, bita, acc, sm.cl, wq, nbuf, lane);
+      pull_claim(p, knext, vb, vb >= 0 ? hb : -1, db, hitw, ob, bitb, acc, sm.cl, wq, nbuf, lane);
     }
-    int h0 = -1, h1 = -1;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q < P0 && h0 < 0 && ((x0[q] >> (u0[q] & 31)) & 1u)) h0 = u0[q];
-      if (q < P1 && h1 < 0 && ((x1[q] >> (u1[q] & 31)) & 1u)) h1 = u1[q];
+    __syncwarp();
+    const uint32_t hits = hitw[lane];
+    if (has) {
+      if (hits) nxt[w] = hits;
+      if ((visw | hits) != vw) p.vis[w] = visw | hits;
     }
-    const long long t0 = e0 - P0, t1 = e1 - P1;
-    h0 = scan_desc_coop(p.tadj, cur, b0, t0, a0 && h0 < 0 && t0 > b0, h0, lane, p.status, p.n);
-    h1 = scan_desc_coop(p.tadj, cur, b1, t1, a1 && h1 < 0 && t1 > b1, h1, lane, p.status, p.n);
-    if (live0) pull_finish(p, nxt, w0, vw0, visw0, v0, h0, b0, e0, knext, acc, sm.cl, wq, nbuf, lane);
-    if (live1) pull_finish(p, nxt, w1, vw1, visw1, v1, h1, b1, e1, knext, acc, sm.cl, wq, nbuf, lane);
+    __syncwarp();
   }
   warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
 }

@@ -123,11 +123,14 @@ extern "C" int bfs_run_static(const int64_t* offsets, const int32_t* adj, int32_
   r.level = level_out;
   r.parent = parent_out;
   if (int e = launch_level_loop(r, s)) return e;
-  BFS_CUDA_TRY(cudaStreamSynchronize(s));
+  // the status words are read on the caller's stream, so that the call waits
+  // for that stream alone and not for other work on the device
   int st[4] = {0, 0, 0, 0};
-  BFS_CUDA_TRY(cudaMemcpy(st, w.status, sizeof(st), cudaMemcpyDeviceToHost));
+  BFS_CUDA_TRY(cudaMemcpyAsync(st, w.status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  BFS_CUDA_TRY(cudaStreamSynchronize(s));
   if (st[0] != 0) {
-    BFS_CUDA_TRY(cudaMemset(base + kOffBarrier, 0, kBarrierBytes + kSmallBytes));
+    BFS_CUDA_TRY(cudaMemsetAsync(base + kOffBarrier, 0, kBarrierBytes + kSmallBytes, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
     return fail(st[0], "bfs_run_static: " + device_status_message(st));
   }
   return BFS_OK;

@@ -1,5 +1,9 @@
 """Full-size checks in the benchmark's launch configurations.
 
+Every root of the scale-26 benchmark is validated, and the scale-24 batched
+traversal row by row; the selector's held-out graphs run under the learned
+selector.
+
 At these sizes the oracle's CSR build would take minutes, so results are checked
 with the oracle's O(m) edge-list validator (`oracle.validate_edges`): zero
 violations means the levels are the hop distances and the parents follow the
@@ -26,41 +30,131 @@ def _cuda():
     require_cuda()
 
 
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1104_4518_gb300",
+                       "selector_weights.bin")
+
+
+class Validations:
+    """Runs `oracle.validate_edges` on host copies of GPU results, a bounded number at
+    a time on a thread pool (the C validator drops the GIL), and collects failures."""
+
+    def __init__(self, el, workers=None):
+        self.el = el
+        self.workers = workers or min(16, os.cpu_count() or 1)
+        self.ex = ThreadPoolExecutor(max_workers=self.workers)
+        self.pending = []
+        self.checked = 0
+
+    def submit(self, what, root, level, parent):
+        if len(self.pending) >= 2 * self.workers:
+            self._drain(self.workers)
+        lv = level.cpu().numpy() if isinstance(level, torch.Tensor) else level
+        pa = parent.cpu().numpy() if isinstance(parent, torch.Tensor) else parent
+        fut = self.ex.submit(oracle.validate_edges, self.el.src, self.el.dst, self.el.n, int(root), lv, pa)
+        self.pending.append((what, fut))
+
+    def _drain(self, keep=0):
+        while len(self.pending) > keep:
+            what, fut = self.pending.pop(0)
+            bad = fut.result()
+            assert bad.sum() == 0, (what, bad.tolist())
+            self.checked += 1
+
+    def finish(self):
+        try:
+            self._drain()
+        finally:
+            self.ex.shutdown()
+        return self.checked
+
+
 def _validate_rows(el, roots, levels, parents):
-    def one(i):
-        return oracle.validate_edges(el.src, el.dst, el.n, int(roots[i]), levels[i], parents[i])
-
-    with ThreadPoolExecutor(max_workers=min(len(roots), os.cpu_count() or 1)) as ex:
-        bad = list(ex.map(one, range(len(roots))))
-    for i, b in enumerate(bad):
-        assert b.sum() == 0, (int(roots[i]), b.tolist())
+    v = Validations(el, workers=min(len(roots), os.cpu_count() or 1))
+    for i in range(len(roots)):
+        v.submit(f"row {i}", roots[i], levels[i], parents[i])
+    v.finish()
 
 
-def test_rmat26_single_root_and_batched_bench_configuration():
-    """R-MAT scale 26 (67 M vertices, 2.1 G CSR entries), graph seed 3 / roots 103: two single-root
-    traversals (heuristic selector) and the bench's 64-root batched traversal.  The batched rows of
-    those two roots equal the single-root results on the device, and the last batched row is
-    validated on its own."""
+@pytest.fixture(scope="module")
+def rmat26():
+    """The scale-26 benchmark graph (67 M vertices, 2.1 G CSR entries; graph seed 3,
+    roots 103) on the device, built by the library's CSR builder."""
     el, roots = inputs.workload_rmat(26, 64, graph_seed=3, root_seed=103)
     g = device_graph_from_edges(el)
-    picks = [0, len(roots) // 2]
-    levels, parents, singles = [], [], []
-    for i in picks:
-        parent, level = bfs.run(g, int(roots[i]))
-        bfs.bfs_sync(g)
-        singles.append((parent, level))
-    pb, lb = bfs.run_batch(g, [int(r) for r in roots])
-    bfs.bfs_sync(g)
-    for i, (parent, level) in zip(picks, singles):
-        assert torch.equal(pb[i], parent) and torch.equal(lb[i], level), f"batched row {i}"
-        levels.append(level.cpu().numpy())
-        parents.append(parent.cpu().numpy())
-    last = len(roots) - 1
-    levels.append(lb[last].cpu().numpy())
-    parents.append(pb[last].cpu().numpy())
-    del pb, lb, singles
+    yield el, [int(r) for r in roots], g
     g.destroy()
-    _validate_rows(el, [int(roots[i]) for i in picks + [last]], levels, parents)
+
+
+def test_rmat26_every_bench_root_and_the_batched_traversal(rmat26):
+    """All 64 benchmark roots at scale 26, heuristic selector (the benchmark's launch
+    configuration): every result validated edge by edge against the oracle's rule.
+    The benchmark's 64-root batched traversal of the same roots gives the same rows,
+    bit for bit, compared on the device."""
+    el, roots, g = rmat26
+    pb, lb = bfs.run_batch(g, roots)
+    bfs.bfs_sync(g)
+    val = Validations(el)
+    deep = 0
+    for i, s in enumerate(roots):
+        parent, level = bfs.run(g, s)
+        bfs.bfs_sync(g)
+        assert torch.equal(pb[i], parent) and torch.equal(lb[i], level), f"batched row {i} (root {s})"
+        deep += int(level.max().item() >= 3)
+        val.submit(f"root {s}", s, level, parent)
+    del pb, lb
+    assert val.finish() == 64
+    assert deep >= 60  # real traversals of the large component, not trivial ones
+
+
+def test_rmat26_forced_variants_schedules_and_learned_selector(rmat26):
+    """At scale 26, four benchmark roots under every forced variant, a random per-level
+    schedule and the learned selector with the shipped weights: each result is
+    bit-identical to the heuristic run of the same root, and those runs are validated
+    edge by edge against the oracle's rule."""
+    el, roots, g = rmat26
+    picks = roots[:4]
+    val = Validations(el)
+    rng = np.random.default_rng(26)
+    bfs.bfs_selector_load(WEIGHTS)
+    try:
+        for s in picks:
+            parent, level = bfs.run(g, s)
+            bfs.bfs_sync(g)
+            val.submit(f"heuristic root {s}", s, level, parent)
+            runs = [(f"forced {v}", bfs.RunOptions(selector=bfs.BFS_SELECT_FORCED, forced_variant=v))
+                    for v in range(bfs.BFS_NUM_VARIANTS)]
+            runs.append(("schedule", bfs.RunOptions(selector=bfs.BFS_SELECT_SCHEDULE,
+                                                    schedule=rng.integers(0, bfs.BFS_NUM_VARIANTS, 16))))
+            runs.append(("learned", bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED)))
+            for name, o in runs:
+                p2, l2 = bfs.run(g, s, o)
+                bfs.bfs_sync(g)
+                assert torch.equal(p2, parent) and torch.equal(l2, level), (name, s)
+    finally:
+        bfs.bfs_selector_set_params(None)
+    assert val.finish() == len(picks)
+
+
+def test_heldout_rmat25_learned_selector():
+    """The selector's held-out R-MAT graph (scale 25, edgefactor 16, graph seed 7,
+    8 roots of seed 107) traversed with the learned selector and the shipped weights:
+    every result validated edge by edge against the oracle's rule."""
+    el = inputs.rmat(25, 16, seed=7)
+    roots = [int(r) for r in inputs.roots(el, 8, 107)]
+    g = device_graph_from_edges(el)
+    bfs.bfs_selector_load(WEIGHTS)
+    val = Validations(el)
+    try:
+        for s in roots:
+            o = bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED, want_counts=True)
+            parent, level = bfs.run(g, s, o)
+            bfs.bfs_sync(g)
+            assert o.nlevels >= 3
+            val.submit(f"learned root {s}", s, level, parent)
+    finally:
+        bfs.bfs_selector_set_params(None)
+        g.destroy()
+    assert val.finish() == len(roots)
 
 
 def test_directed_rmat22_validated():
@@ -109,13 +203,24 @@ def test_rmat24_batched_64_roots():
     _validate_rows(el, roots, lv, pa)
 
 
-def test_grid256_closed_form():
-    """The 256^3 grid from the corner (766 levels): level = x + y + z, parent by the max-id rule."""
+@pytest.mark.parametrize("selector", ["heuristic", "learned"])
+def test_grid256_closed_form(selector):
+    """The 256^3 grid from the corner (766 levels; the selector's held-out grid):
+    level = x + y + z and the max-id parent, under the heuristic and under the learned
+    selector with the shipped weights."""
     N = 256
     el = inputs.grid3d(N)
     g = device_graph_from_edges(el)
-    parent, level = bfs.run(g, 0)
-    bfs.bfs_sync(g)
+    learned = selector == "learned"
+    if learned:
+        bfs.bfs_selector_load(WEIGHTS)
+    try:
+        parent, level = bfs.run(g, 0, bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED) if learned else None)
+        bfs.bfs_sync(g)
+    finally:
+        if learned:
+            bfs.bfs_selector_set_params(None)
+        g.destroy()
     level, parent = level.cpu().numpy(), parent.cpu().numpy()
     v = np.arange(N ** 3, dtype=np.int64)
     x, y, z = v % N, (v // N) % N, v // (N * N)

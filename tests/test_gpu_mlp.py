@@ -5,8 +5,11 @@ Tolerance: float32 kernels against float64 arithmetic on the same float32 inputs
 Each output is a dot product of at most 64 terms of magnitude <= ~1 passed through
 three layers; float32 rounding (2^-24 relative per operation) accumulated over
 ~200 dependent operations stays below 1e-5 relative, so forward outputs are
-checked at rtol 1e-5 / atol 1e-5, and gradients (sums over a batch of such terms)
-at rtol 1e-4 / atol 1e-6."""
+checked at rtol 1e-5 / atol 1e-5.  A gradient entry is a sum over the batch whose
+terms can cancel, so its plain relative error is unbounded; it is checked at 1e-5
+relative to its magnitude scale (`oracle.mlp.grad_scale`: the same sums over
+absolute values, the quantity floating-point rounding error is proportional to).
+A float32 NumPy evaluation stays below 3e-7 of that scale on these inputs."""
 import numpy as np
 import pytest
 import torch
@@ -57,7 +60,10 @@ def test_loss_and_gradient(B):
                           grad, loss)
     ref_loss, ref_grad = mlp.loss_and_grad(w.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
     np.testing.assert_allclose(loss.item(), ref_loss, rtol=1e-5)
-    np.testing.assert_allclose(grad.cpu().numpy(), ref_grad, rtol=1e-4, atol=1e-6)
+    scale = mlp.grad_scale(w.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    err = np.abs(grad.cpu().numpy().astype(np.float64) - ref_grad)
+    worst = int(np.argmax(err - 1e-5 * scale))
+    assert np.all(err <= 1e-5 * scale + 1e-12), (worst, err[worst], scale[worst])
     # deterministic: a second evaluation is bit-identical
     g2 = torch.empty_like(grad)
     bfs.bfs_mlp_loss_grad(torch.from_numpy(w).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(),

@@ -79,3 +79,40 @@ def test_features_scaling():
     assert f.shape == (12,)
     assert f[0] == 20 / 32 and f[1] == 24 / 32 and f[2] == 2 / 10
     assert f[7] == 0.5 and f[8] == 0.5 and np.allclose(f[9:], [0.9, 0.09, 0.01])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_grad_scale_bounds_the_gradient(seed):
+    """The magnitude scale is never below |gradient| (triangle inequality), and
+    equals it when every operand is non-negative and the targets are zero, so
+    that no term of any sum (nor the output error Y - T) has a negative sign."""
+    rng = np.random.default_rng(seed)
+    w = rand_params(seed)
+    X = rng.standard_normal((9, 12))
+    T = rng.standard_normal((9, 4))
+    _, g = mlp.loss_and_grad(w, X, T)
+    assert np.all(mlp.grad_scale(w, X, T) >= np.abs(g) - 1e-15)
+    wp = np.abs(w) + 0.01
+    Xp = rng.random((9, 12))
+    Y, _ = mlp.forward(wp, Xp)
+    Tp = np.zeros_like(Y)
+    assert np.all(Y > 0)
+    _, gp = mlp.loss_and_grad(wp, Xp, Tp)
+    np.testing.assert_allclose(mlp.grad_scale(wp, Xp, Tp), gp, rtol=1e-12, atol=0)
+
+
+def test_grad_scale_catches_a_float32_error_that_rtol_alone_would_excuse():
+    """A float32 evaluation of the gradient lies well within 1e-5 of the scale; a
+    perturbation of one entry by 1e-4 of its scale is outside it."""
+    rng = np.random.default_rng(5)
+    w = rand_params(5).astype(np.float32).astype(np.float64)
+    X = rng.random((64, 12)).astype(np.float32).astype(np.float64)
+    T = (3 * rng.standard_normal((64, 4))).astype(np.float32).astype(np.float64)
+    _, g = mlp.loss_and_grad(w, X, T)
+    s = mlp.grad_scale(w, X, T)
+    g32 = g.astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(g32 - g) <= 1e-5 * s + 1e-12)
+    i = int(np.argmax(s))
+    bad = g.copy()
+    bad[i] += 1e-4 * s[i]
+    assert not np.all(np.abs(bad - g) <= 1e-5 * s + 1e-12)
