@@ -17,6 +17,8 @@ Contents
     in pure Python (small inputs only): each level is the sparse matrix-sparse
     vector product over the (select2nd, max) semiring, masked by the parents
     vector, followed by the parent update and the frontier replacement.
+  - `dcsc_tiles`: the 2D blocks of Sec. 3.2 in the doubly compressed sparse
+    column form of Sec. 4.1 (arrays IR, JC, CP per block), for any block sizes.
   - `mlp` (separate module): the variant-selector network in float64 NumPy.
 """
 from __future__ import annotations
@@ -287,3 +289,42 @@ def bfs_spmsv(rows, s: int):
         f = {v: v for v in t}
         k += 1
     return level, parent
+
+
+# ---------------- 2D blocks in DCSC (Sec. 3.2, Sec. 4.1) ----------------
+
+def dcsc_tiles(g: CSR, rows_per_block: int, cols_per_block: int) -> dict:
+    """The entries of `g` split into a 2D grid of blocks, each in DCSC form.
+
+    Entry (v, u) is "u in row v of g" (row v lists the candidate parents u of v,
+    the transposed orientation Algorithm 3 multiplies with).  Block (rb, cb)
+    holds the entries with v // rows_per_block == rb and u // cols_per_block ==
+    cb; blocks are numbered t = rb * ncb + cb.  DCSC of a block (Sec. 4.1): JC
+    lists the block's non-empty columns in ascending order, CP the start of
+    each column's row ids, IR the row ids, ascending within a column; ids are
+    local to the block (v mod rows_per_block, u mod cols_per_block).  Returned
+    as flat arrays over all blocks in block order: tdir_jc / tdir_ir (first
+    column / first entry of each block, plus one end entry), jc, cp (relative
+    to the block's first entry) and ir.  A library sort orders the entries by
+    (block, column, row); the rest follows the definition.
+    """
+    n = g.n
+    nrb = (n + rows_per_block - 1) // rows_per_block
+    ncb = (n + cols_per_block - 1) // cols_per_block
+    T = nrb * ncb
+    v = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.offsets))
+    u = g.adj.astype(np.int64)
+    t = (v // rows_per_block) * ncb + u // cols_per_block
+    order = np.lexsort((v, u, t))
+    v, u, t = v[order], u[order], t[order]
+    ir = v % rows_per_block
+    ul = u % cols_per_block
+    new_col = np.ones(v.shape[0], dtype=bool)
+    new_col[1:] = (t[1:] != t[:-1]) | (u[1:] != u[:-1])
+    starts = np.nonzero(new_col)[0]
+    tdir_ir = np.searchsorted(t, np.arange(T + 1), side="left").astype(np.int64)
+    tdir_jc = np.searchsorted(t[starts], np.arange(T + 1), side="left").astype(np.int64)
+    jc = ul[starts]
+    cp = starts - tdir_ir[t[starts]]
+    return {"nrb": nrb, "ncb": ncb, "ntiles": T, "nzc": int(starts.shape[0]), "tdir_jc": tdir_jc,
+            "tdir_ir": tdir_ir, "jc": jc.astype(np.int64), "cp": cp.astype(np.int64), "ir": ir.astype(np.int64)}
