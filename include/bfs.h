@@ -76,6 +76,7 @@ BFS_API int bfs_bounds_checked(void); /* 1 in the bounds-checking build, 0 other
 #define BFS_HOST_PTRS 0x1u /* the input (graph create) or output (run) pointers are host memory */
 #define BFS_VALIDATE 0x2u  /* graph create: check the CSR on the device before accepting it */
 #define BFS_DIRECTED 0x4u  /* graph create: the arcs are directed (see below) */
+#define BFS_HOST_ASYNC 0x8u /* bfs_run with BFS_HOST_PTRS: return once the copies are enqueued (see bfs_run) */
 
 /* Per-level expansion variants (each gives identical levels and parents). */
 typedef enum bfs_variant {
@@ -83,7 +84,9 @@ typedef enum bfs_variant {
   BFS_VARIANT_TD_WARP = 1,   /* top-down SpMSV, one warp per frontier vertex */
   BFS_VARIANT_TD_BINNED = 2, /* top-down SpMSV, thread / warp / CTA per vertex by degree bin */
   BFS_VARIANT_PULL = 3,      /* dense-frontier SpMV: unvisited rows scan their adjacency, largest id first */
-  BFS_NUM_VARIANTS = 4
+  BFS_VARIANT_TILED = 4,     /* dense-frontier SpMV over the 2D tiles of Sec. 3.2 stored as DCSC (Sec. 4.1),
+                                with tile-local frontier and row slices in shared memory (bfs_graph_tiles) */
+  BFS_NUM_VARIANTS = 5
 } bfs_variant;
 
 /* How bfs_run picks the variant of each level. */
@@ -138,7 +141,8 @@ typedef struct bfs_opts {
   int64_t* edges_out;        /* host int64; when set, the call synchronises and writes the TEPS edge
                                 count of the traversal (undirected edges inside the reached set) */
   uint32_t spin_limit;       /* device wait limit in polls (0 = default, about one second) */
-  uint32_t flags;            /* BFS_HOST_PTRS: parent_out/level_out are host memory */
+  uint32_t flags;            /* BFS_HOST_PTRS: parent_out/level_out are host memory;
+                                BFS_HOST_ASYNC with it: bfs_run does not wait for the copies */
 } bfs_opts;
 
 typedef struct bfs_graph bfs_graph;
@@ -214,6 +218,14 @@ BFS_API void bfs_graph_destroy(bfs_graph* g);
  * Asynchronous unless opts asks for statistics or host outputs.  Device-side
  * failures (BFS_ERR_TIMEOUT; BFS_ERR_BOUNDS in the bounds-checking build) are
  * returned by bfs_sync or by a synchronising call; until then further runs on the same stream do no work.
+ * Host outputs (opts->flags BFS_HOST_PTRS): the traversal writes a device
+ * staging buffer of the (graph, stream) workspace, then the library copies it
+ * to the host arrays and waits.  With BFS_HOST_ASYNC as well, the call returns
+ * once the copies are enqueued on a copy stream of the workspace, and the host
+ * arrays are complete after bfs_sync(g, stream) (the host arrays must stay
+ * valid until then; pinned memory gives the full copy bandwidth).  The
+ * workspace then alternates between two staging buffers, so that the copies
+ * of one traversal overlap the next traversal on the same stream.
  */
 BFS_API int bfs_run(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_out,
             const bfs_opts* opts, void* stream);
@@ -273,8 +285,45 @@ BFS_API int bfs_run_ragged(bfs_graph* u, const int32_t* sources, int32_t* const*
 BFS_API int bfs_run_static(const int64_t* offsets, const int32_t* adj, int32_t n, int64_t nnz, int32_t source,
                            int32_t* parent_out, int32_t* level_out, void* stream);
 
-/* Waits for the stream and returns (and clears) the device status of the last
- * run enqueued on it for graph g. */
+/*
+ * The 2D tiles of g that BFS_VARIANT_TILED walks: Sec. 3.2's 2D blocks of the
+ * adjacency matrix, each stored in the doubly compressed sparse column form of
+ * Sec. 4.1 (IR row ids indexed by the parallel arrays JC of non-empty column
+ * ids and CP of column pointers).  Row blocks hold 2^rb_bits vertices v (the
+ * vertices a pull level may reach), column blocks 2^cb_bits vertices u (their
+ * candidate parents); tile t = rb * ncb + cb holds the entries (v, u) of v's
+ * in-row (its row, for an undirected graph) with v >> rb_bits == rb and
+ * u >> cb_bits == cb.  The tiles are built on the device when g has none, or
+ * when rb_bits / cb_bits (each in [5, 16], or 0 for the default: cb_bits 16,
+ * rb_bits so that there are about 4 row blocks per SM, within [8, 16]) differ
+ * from those of g's current tiles; other values give BFS_ERR_INVALID_ARG.  A
+ * traversal that uses BFS_VARIANT_TILED builds the default tiles if g has none.
+ * Rebuilding must not overlap a traversal of g on another stream.  On return
+ * *info holds the layout and DEVICE pointers owned by g, valid until the tiles
+ * are rebuilt or g is destroyed:
+ *   tdir_jc, tdir_ir (int64[ntiles + 1]): first column / first entry of tile t;
+ *   jc (uint16[nzc]): tile-local ids of each tile's non-empty columns, ascending;
+ *   cp (uint32[nzc]): first entry of each column relative to its tile's first
+ *     entry (a column ends where the next column of its tile starts, or where
+ *     its tile ends);
+ *   ir (uint16[nnz]): tile-local row ids, ascending within each column.
+ * Synchronises the stream.  The tiles take about 8 bytes per CSR entry.
+ */
+typedef struct bfs_tile_info {
+  int32_t rb_bits, cb_bits; /* log2 of the rows / columns per tile */
+  int32_t nrb, ncb;         /* row blocks, column blocks */
+  int64_t ntiles, nzc, nnz; /* nrb * ncb, non-empty (tile, column) pairs, entries */
+  const int64_t* tdir_jc;
+  const int64_t* tdir_ir;
+  const uint16_t* jc;
+  const uint32_t* cp;
+  const uint16_t* ir;
+} bfs_tile_info;
+BFS_API int bfs_graph_tiles(bfs_graph* g, int32_t rb_bits, int32_t cb_bits, bfs_tile_info* info, void* stream);
+
+/* Waits for the stream (and for the copies of asynchronous host outputs of
+ * runs on it) and returns (and clears) the device status of the last run
+ * enqueued on it for graph g. */
 BFS_API int bfs_sync(bfs_graph* g, void* stream);
 
 /* Tuning of a graph (copied in / out). */
@@ -296,9 +345,11 @@ BFS_API int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs
  * Network 12 -> 64 -> 64 -> 4, ReLU, float32, parameters packed flat as
  * W1[12][64], b1[64], W2[64][64], b2[64], W3[64][4], b3[4] (5,252 floats).
  * Inputs are the level features listed with bfs_level_features; outputs are
- * predicted log2 level times in microseconds of the four variants, and the
- * selector takes the argmin.  (The paper's counterpart is its choice between
- * two SpMSV accumulators by concurrency, Sec. 4.2.)
+ * predicted log2 level times in microseconds of the four variants
+ * BFS_VARIANT_TD_THREAD .. BFS_VARIANT_PULL, and the selector takes the
+ * argmin (BFS_VARIANT_TILED is chosen only by BFS_SELECT_FORCED or a
+ * schedule).  (The paper's counterpart is its choice between two SpMSV
+ * accumulators by concurrency, Sec. 4.2.)
  */
 #define BFS_MLP_PARAMS 5252
 #define BFS_MLP_IN 12
@@ -324,8 +375,9 @@ BFS_API int bfs_selector_train(float* params, const float* X, const float* T, in
 
 /*
  * Training samples for the selector network from traversals of graph g: for
- * every root (host array) the traversal runs `reps` times with each variant
- * forced at every level, and for every level k one row is written:
+ * every root (host array) the traversal runs `reps` times with each of the
+ * network's four variants forced at every level, and for every level k one
+ * row is written:
  * X[row][0..11] = the level's features (bfs_level_features) and
  * T[row][v] = log2 of the median time in microseconds of level k under
  * variant v (host float arrays of max_rows rows).  *rows_out receives the

@@ -38,13 +38,15 @@ BFS_ERR_BOUNDS = 7
 BFS_HOST_PTRS = 0x1
 BFS_VALIDATE = 0x2
 BFS_DIRECTED = 0x4
+BFS_HOST_ASYNC = 0x8
 
 BFS_VARIANT_TD_THREAD = 0
 BFS_VARIANT_TD_WARP = 1
 BFS_VARIANT_TD_BINNED = 2
 BFS_VARIANT_PULL = 3
-BFS_NUM_VARIANTS = 4
-VARIANT_NAMES = ("td_thread", "td_warp", "td_binned", "pull")
+BFS_VARIANT_TILED = 4
+BFS_NUM_VARIANTS = 5
+VARIANT_NAMES = ("td_thread", "td_warp", "td_binned", "pull", "tiled")
 
 BFS_SELECT_HEURISTIC = 0
 BFS_SELECT_LEARNED = 1
@@ -80,6 +82,13 @@ class bfs_tuning(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class bfs_tile_info(ctypes.Structure):
+    _fields_ = [("rb_bits", ctypes.c_int32), ("cb_bits", ctypes.c_int32), ("nrb", ctypes.c_int32),
+                ("ncb", ctypes.c_int32), ("ntiles", ctypes.c_int64), ("nzc", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("tdir_jc", ctypes.c_void_p), ("tdir_ir", ctypes.c_void_p), ("jc", ctypes.c_void_p),
+                ("cp", ctypes.c_void_p), ("ir", ctypes.c_void_p)]
+
+
 class bfs_opts(ctypes.Structure):
     _fields_ = [("selector", ctypes.c_int32), ("forced_variant", ctypes.c_int32),
                 ("schedule", ctypes.POINTER(ctypes.c_int32)), ("schedule_len", ctypes.c_int32),
@@ -108,6 +117,7 @@ def _declare(lib):
                            ctypes.POINTER(bfs_opts), vp],
         "bfs_sync": [vp, vp],
         "bfs_run_static": [vp, vp, i32, i64, i32, vp, vp, vp],
+        "bfs_graph_tiles": [vp, i32, i32, ctypes.POINTER(bfs_tile_info), vp],
         "bfs_set_tuning": [vp, ctypes.POINTER(bfs_tuning)],
         "bfs_get_tuning": [vp, ctypes.POINTER(bfs_tuning)],
         "bfs_autotune": [vp, ctypes.POINTER(i32), i32, ctypes.POINTER(bfs_tuning), vp],
@@ -272,13 +282,48 @@ def bfs_graph_copy_csr(g: Graph, device: bool = True):
     return off, adj[:nnz]
 
 
+class _DeviceArray:
+    """A view of library-owned device memory for torch.as_tensor (only ever copied from)."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3}
+
+
+def _device_copy_to_host(ptr, count: int, typestr: str, view_dtype):
+    torch = _torch()
+    if count <= 0:
+        return np.zeros(0, dtype=view_dtype)
+    t = torch.as_tensor(_DeviceArray(ptr, count, typestr), device="cuda")
+    return t.cpu().numpy().view(view_dtype).copy()
+
+
+def bfs_graph_tiles(g: Graph, rb_bits: int = 0, cb_bits: int = 0, stream=None, host_copy: bool = True) -> dict:
+    """The graph's 2D DCSC tiles (built when absent or when the bits differ; 0 = default).
+
+    Returns the layout and, with host_copy, NumPy copies of tdir_jc, tdir_ir
+    (int64), jc (uint16), cp (uint32) and ir (uint16)."""
+    info = bfs_tile_info()
+    _check(lib().bfs_graph_tiles(g.handle, int(rb_bits), int(cb_bits), ctypes.byref(info), _stream_handle(stream)))
+    out = {f: getattr(info, f) for f in ("rb_bits", "cb_bits", "nrb", "ncb", "ntiles", "nzc", "nnz")}
+    if host_copy:
+        T, nzc, nnz = info.ntiles, info.nzc, info.nnz
+        out["tdir_jc"] = _device_copy_to_host(info.tdir_jc, T + 1, "<i8", np.int64)
+        out["tdir_ir"] = _device_copy_to_host(info.tdir_ir, T + 1, "<i8", np.int64)
+        out["jc"] = _device_copy_to_host(info.jc, nzc, "<i2", np.uint16)
+        out["cp"] = _device_copy_to_host(info.cp, nzc, "<i4", np.uint32)
+        out["ir"] = _device_copy_to_host(info.ir, nnz, "<i2", np.uint16)
+    return out
+
+
 # ---------------- options ----------------
 
 class RunOptions:
     """Python side of bfs_opts; keeps the buffers the C struct points into alive."""
 
     def __init__(self, selector: int = BFS_SELECT_HEURISTIC, forced_variant: int = 0, schedule=None,
-                 stats_levels: int = 0, want_counts: bool = False, spin_limit: int = 0, host_outputs=False):
+                 stats_levels: int = 0, want_counts: bool = False, spin_limit: int = 0, host_outputs=False,
+                 host_async=False):
         self.c = bfs_opts()
         self.c.selector = selector
         self.c.forced_variant = forced_variant
@@ -298,7 +343,7 @@ class RunOptions:
             self.c.nlevels_out = ctypes.pointer(self._nl)
             self.c.edges_out = ctypes.pointer(self._edges)
         self.c.spin_limit = spin_limit
-        self.c.flags = BFS_HOST_PTRS if host_outputs else 0
+        self.c.flags = (BFS_HOST_PTRS if host_outputs else 0) | (BFS_HOST_ASYNC if host_outputs and host_async else 0)
 
     @property
     def nlevels(self) -> int:

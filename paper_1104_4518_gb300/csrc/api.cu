@@ -92,9 +92,14 @@ void free_workspace(Workspace* w) {
   void* ptrs[] = {w->queue[0], w->queue[1], w->queue[2], w->queue[3], w->bits[0], w->bits[1], w->bits[2],
                   w->bits[3], w->vis, w->chunks[0], w->chunks[1], w->ctr, w->barrier, w->status, w->stats, w->misc,
                   w->edges_out, w->schedule, w->sources, w->tmp_level, w->tmp_parent, w->bset[0], w->bset[1],
-                  w->bset[2], w->bvis, w->bscr, w->part_out};
+                  w->bset[2], w->bvis, w->bscr, w->part_out, w->tmp2_level, w->tmp2_parent};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (w->copy_stream) cudaStreamDestroy(w->copy_stream);
+  for (int i = 0; i < 2; ++i) {
+    if (w->staged_ev[i]) cudaEventDestroy(w->staged_ev[i]);
+    if (w->copied_ev[i]) cudaEventDestroy(w->copied_ev[i]);
+  }
   if (w->h_stage) cudaFreeHost(w->h_stage);
   if (w->stage_ev) cudaEventDestroy(w->stage_ev);
   delete w;
@@ -147,11 +152,33 @@ int get_workspace(bfs_graph* g, cudaStream_t s, Workspace** out) {
   return BFS_OK;
 }
 
+// Staging pair 0 is shared by synchronous host outputs, ragged runs and
+// asynchronous host outputs: work that rewrites it on stream s first waits
+// until its last asynchronous copy-out has read it.
+static int stage0_ready(Workspace* w, cudaStream_t s) {
+  if (w->copy_stream) BFS_CUDA_TRY(cudaStreamWaitEvent(s, w->copied_ev[0], 0));
+  return BFS_OK;
+}
+
 int ensure_tmp_outputs(bfs_graph* g, Workspace* w) {
   if (w->tmp_level) return BFS_OK;
   const size_t nq = sizeof(int32_t) * (size_t)g->n;
   if (int e = dev_alloc((void**)&w->tmp_level, nq, "union-space levels")) return e;
   if (int e = dev_alloc((void**)&w->tmp_parent, nq, "union-space parents")) return e;
+  return BFS_OK;
+}
+
+int ensure_async_outputs(bfs_graph* g, Workspace* w) {
+  if (int e = ensure_tmp_outputs(g, w)) return e;
+  if (w->copy_stream) return BFS_OK;
+  const size_t nq = sizeof(int32_t) * (size_t)g->n;
+  if (int e = dev_alloc((void**)&w->tmp2_level, nq, "second staging levels")) return e;
+  if (int e = dev_alloc((void**)&w->tmp2_parent, nq, "second staging parents")) return e;
+  for (int i = 0; i < 2; ++i) {
+    BFS_CUDA_TRY(cudaEventCreateWithFlags(&w->staged_ev[i], cudaEventDisableTiming));
+    BFS_CUDA_TRY(cudaEventCreateWithFlags(&w->copied_ev[i], cudaEventDisableTiming));
+  }
+  BFS_CUDA_TRY(cudaStreamCreateWithFlags(&w->copy_stream, cudaStreamNonBlocking));
   return BFS_OK;
 }
 
@@ -501,7 +528,43 @@ void bfs_graph_destroy(bfs_graph* g) {
   if (g->d_part_base) cudaFree(g->d_part_base);
   if (g->d_dead) cudaFree(g->d_dead);
   if (g->d_big) cudaFree(g->d_big);
+  free_tiles(g->tiles);
   delete g;
+}
+
+int bfs_graph_tiles(bfs_graph* g, int32_t rb_bits, int32_t cb_bits, bfs_tile_info* info, void* stream) {
+  NvtxRange nvtx_range("bfs_graph_tiles");
+  if (int e = check_graph(g)) return e;
+  if (!info) return fail(BFS_ERR_INVALID_ARG, "bfs_graph_tiles: NULL info");
+  if ((rb_bits != 0 && (rb_bits < 5 || rb_bits > 16)) || (cb_bits != 0 && (cb_bits < 5 || cb_bits > 16)))
+    return fail(BFS_ERR_INVALID_ARG, "bfs_graph_tiles: rb_bits and cb_bits must be 0 or in [5, 16]");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceInfo di;
+  if (int e = current_device_info(&di)) return e;
+  std::lock_guard<std::mutex> lk(g->mu);
+  const int rbb = rb_bits ? rb_bits : default_tile_rb_bits(g->n, di.sm_count);
+  const int cbb = cb_bits ? cb_bits : 16;
+  if (g->tiles == nullptr || g->tiles->rb_bits != rbb || g->tiles->cb_bits != cbb) {
+    BFS_CUDA_TRY(cudaDeviceSynchronize());  // no traversal may still read the old tiles
+    TileSet* ts = nullptr;
+    if (int e = build_tiles(g, di.sm_count, rbb, cbb, s, &ts)) return e;
+    free_tiles(g->tiles);
+    g->tiles = ts;
+  }
+  const TileSet* t = g->tiles;
+  info->rb_bits = t->rb_bits;
+  info->cb_bits = t->cb_bits;
+  info->nrb = t->nrb;
+  info->ncb = t->ncb;
+  info->ntiles = t->ntiles;
+  info->nzc = t->nzc;
+  info->nnz = g->nnz;
+  info->tdir_jc = t->tdir_jc;
+  info->tdir_ir = t->tdir_ir;
+  info->jc = t->jc;
+  info->cp = t->cp;
+  info->ir = t->ir;
+  return BFS_OK;
 }
 
 static int fill_run_options(const bfs_opts* opts, RunRequest& r) {
@@ -559,8 +622,19 @@ int bfs_run(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_ou
   r.nsources = 1;
   if (int e = fill_run_options(opts, r)) return e;
   const bool host = opts && (opts->flags & BFS_HOST_PTRS);
-  if (host) {
+  const bool async = host && (opts->flags & BFS_HOST_ASYNC);
+  int stage = 0;
+  if (async) {
+    // alternate staging pairs; a pair is rewritten only after its last copy-out
+    if (int e = ensure_async_outputs(g, w)) return e;
+    stage = w->stage_next;
+    w->stage_next ^= 1;
+    BFS_CUDA_TRY(cudaStreamWaitEvent(s, w->copied_ev[stage], 0));
+    r.level = stage ? w->tmp2_level : w->tmp_level;
+    r.parent = stage ? w->tmp2_parent : w->tmp_parent;
+  } else if (host) {
     if (int e = ensure_tmp_outputs(g, w)) return e;
+    if (int e = stage0_ready(w, s)) return e;
     r.level = w->tmp_level;
     r.parent = w->tmp_parent;
   } else {
@@ -568,8 +642,17 @@ int bfs_run(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_ou
     r.parent = parent_out;
   }
   if (int e = launch_level_loop(r, s)) return e;
+  const size_t nb = sizeof(int32_t) * (size_t)g->n;
+  if (async) {
+    BFS_CUDA_TRY(cudaEventRecord(w->staged_ev[stage], s));
+    BFS_CUDA_TRY(cudaStreamWaitEvent(w->copy_stream, w->staged_ev[stage], 0));
+    BFS_CUDA_TRY(cudaMemcpyAsync(level_out, r.level, nb, cudaMemcpyDeviceToHost, w->copy_stream));
+    BFS_CUDA_TRY(cudaMemcpyAsync(parent_out, r.parent, nb, cudaMemcpyDeviceToHost, w->copy_stream));
+    BFS_CUDA_TRY(cudaEventRecord(w->copied_ev[stage], w->copy_stream));
+    if (opts->stats || opts->nlevels_out || opts->edges_out) return finish_run(w, opts, s, 0);
+    return BFS_OK;
+  }
   if (host) {
-    const size_t nb = sizeof(int32_t) * (size_t)g->n;
     BFS_CUDA_TRY(cudaMemcpyAsync(level_out, w->tmp_level, nb, cudaMemcpyDeviceToHost, s));
     BFS_CUDA_TRY(cudaMemcpyAsync(parent_out, w->tmp_parent, nb, cudaMemcpyDeviceToHost, s));
   }
@@ -672,6 +755,7 @@ int bfs_run_ragged(bfs_graph* u, const int32_t* sources, int32_t* const* parent_
   r.h_sources = usrc.data();
   r.nsources = parts;
   if (int e = fill_run_options(opts, r)) return e;
+  if (int e = stage0_ready(w, s)) return e;
   r.level = w->tmp_level;
   r.parent = w->tmp_parent;
   r.part_out = w->part_out;
@@ -694,6 +778,7 @@ int bfs_sync(bfs_graph* g, void* stream) {
     BFS_CUDA_TRY(cudaStreamSynchronize(s));
     return BFS_OK;
   }
+  if (w->copy_stream) BFS_CUDA_TRY(cudaStreamSynchronize(w->copy_stream));  // asynchronous host outputs
   return read_status(w, s);
 }
 
@@ -727,10 +812,10 @@ int bfs_selector_collect(bfs_graph* g, const int32_t* roots, int32_t nroots, int
   int rc = BFS_OK;
   for (int i = 0; i < nroots && !rc; ++i) {
     // times[v][rep][level]
-    std::vector<std::vector<std::vector<double>>> times(BFS_NUM_VARIANTS);
+    std::vector<std::vector<std::vector<double>>> times(BFS_MLP_OUT);  // the network's variants
     std::vector<bfs_level_stat> first;
     int nl = -1;
-    for (int v = 0; v < BFS_NUM_VARIANTS && !rc; ++v) {
+    for (int v = 0; v < BFS_MLP_OUT && !rc; ++v) {
       for (int rep = 0; rep < reps + 1 && !rc; ++rep) {  // the first run warms up
         bfs_opts o{};
         o.selector = BFS_SELECT_FORCED;
@@ -757,7 +842,7 @@ int bfs_selector_collect(bfs_graph* g, const int32_t* roots, int32_t nroots, int
       const int64_t bins[3] = {s.bin_count[0], s.bin_count[1], s.bin_count[2]};
       bfs_level_features(g->n, g->nnz, k, s.frontier_count, s.frontier_edges, s.unvisited_count, s.unvisited_edges,
                          bins, X + (size_t)rows * BFS_MLP_IN);
-      for (int v = 0; v < BFS_NUM_VARIANTS; ++v) {
+      for (int v = 0; v < BFS_MLP_OUT; ++v) {
         std::vector<double> samples;
         for (auto& run : times[v]) samples.push_back(run[k]);
         std::sort(samples.begin(), samples.end());

@@ -392,6 +392,50 @@ int bits_for(int32_t n) {
 
 }  // namespace
 
+int radix_sort_u64(uint64_t* keys, uint64_t* alt, long long N, int lo_bit, int hi_bit, cudaStream_t s,
+                   uint64_t** sorted) {
+  *sorted = keys;
+  if (N <= 0 || lo_bit >= hi_bit) return BFS_OK;
+  const long long ntiles = (N + kTile - 1) / kTile;
+  const long long hsize = ntiles * kRadix;
+  uint32_t* hist = nullptr;
+  int64_t* hoff = nullptr;
+  if (int e = dev_alloc((void**)&hist, sizeof(uint32_t) * hsize, "radix histogram")) return e;
+  if (int e = dev_alloc((void**)&hoff, sizeof(int64_t) * hsize, "radix offsets")) {
+    cudaFree(hist);
+    return e;
+  }
+  uint64_t* a = keys;
+  uint64_t* b = alt;
+  int rc = BFS_OK;
+  for (int shift = lo_bit; shift < hi_bit && !rc; shift += 8) {
+    radix_hist_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(a, N, shift, hist, ntiles);
+    ScanInput si;
+    si.u32 = hist;
+    long long tot = 0;
+    rc = exclusive_scan(si, hsize, hoff, s, &tot);
+    if (rc) break;
+    radix_scatter_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(a, b, N, shift, hoff, ntiles);
+    uint64_t* t = a;
+    a = b;
+    b = t;
+  }
+  cudaError_t err = cudaGetLastError();
+  if (!rc && err == cudaSuccess) err = cudaStreamSynchronize(s);
+  cudaFree(hist);
+  cudaFree(hoff);
+  if (rc) return rc;
+  if (err != cudaSuccess) return cuda_fail(err, "radix sort");
+  *sorted = a;
+  return BFS_OK;
+}
+
+int exclusive_scan_u32(const uint32_t* in, long long N, int64_t* out, cudaStream_t s, long long* total) {
+  ScanInput si;
+  si.u32 = in;
+  return exclusive_scan(si, N, out, s, total);
+}
+
 int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, int mode,
                          cudaStream_t s, int64_t** d_off_out, int32_t** d_adj_out, int64_t* nnz_out) {
   DeviceInfo di;

@@ -78,6 +78,14 @@ struct Workspace {
   int32_t* sources = nullptr;       // device, up to kMaxSources
   int32_t* tmp_level = nullptr;     // union-space outputs (ragged / host outputs), lazily
   int32_t* tmp_parent = nullptr;
+  // asynchronous host outputs: a second staging pair, the copy stream, and per
+  // staging pair the events "traversal written" and "copied out"
+  int32_t* tmp2_level = nullptr;
+  int32_t* tmp2_parent = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t staged_ev[2] = {nullptr, nullptr};
+  cudaEvent_t copied_ev[2] = {nullptr, nullptr};
+  int stage_next = 0;
   // batched (64-root bitset) state, lazily
   uint64_t* bset[3] = {nullptr, nullptr, nullptr};
   uint64_t* bvis = nullptr;
@@ -97,6 +105,28 @@ constexpr int kMaxSources = 4096;
 
 }  // namespace bfsint
 
+namespace bfsint {
+// Hypersparse 2D tiles of the in-adjacency (rows = the vertices a pull level
+// reaches, columns = their candidate parents), in the doubly compressed
+// sparse column form of Sec. 4.1: rows are split into blocks of 2^rb_bits
+// vertices and columns into blocks of 2^cb_bits; tile t = rb * ncb + cb holds
+// the entries (v, u) with v in row block rb and u in column block cb.  Within
+// a tile, jc lists the tile-local ids of the non-empty columns (ascending), cp
+// the start of each column's rows relative to the tile's first entry, and ir
+// the tile-local row ids (ascending within a column).  tdir_jc[t] / tdir_ir[t]
+// give tile t's first column / first entry (T + 1 entries each).
+struct TileSet {
+  int rb_bits = 0, cb_bits = 0;
+  int32_t nrb = 0, ncb = 0;
+  int64_t ntiles = 0, nzc = 0;
+  uint16_t* jc = nullptr;
+  uint32_t* cp = nullptr;
+  uint16_t* ir = nullptr;
+  int64_t* tdir_jc = nullptr;
+  int64_t* tdir_ir = nullptr;
+};
+}  // namespace bfsint
+
 struct bfs_graph {
   int32_t n = 0;
   int64_t nnz = 0;
@@ -112,6 +142,7 @@ struct bfs_graph {
   std::vector<int64_t> part_base;  // parts + 1 entries (union graphs)
   int64_t* d_part_base = nullptr;
   bfs_tuning tuning{};
+  bfsint::TileSet* tiles = nullptr;  // built on the first run that may use the tiled variant
   int device = 0;
   std::mutex mu;
   std::vector<bfsint::Workspace*> ws;
@@ -126,6 +157,7 @@ int get_workspace(bfs_graph* g, cudaStream_t s, Workspace** out);
 void free_workspace(Workspace* w);
 int ensure_batch_state(bfs_graph* g, Workspace* w);
 int ensure_tmp_outputs(bfs_graph* g, Workspace* w);
+int ensure_async_outputs(bfs_graph* g, Workspace* w);
 
 // Effective tuning with defaults filled in.
 bfs_tuning effective_tuning(const bfs_graph* g);
@@ -135,6 +167,20 @@ bfs_tuning effective_tuning(const bfs_graph* g);
 // mode 0: undirected (both arcs of every edge), 1: arcs src -> dst, 2: arcs dst -> src.
 int build_csr_from_edges(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n, int mode,
                          cudaStream_t s, int64_t** d_off, int32_t** d_adj, int64_t* nnz);
+// Stable least-significant-digit radix sort of N 64-bit keys on bits
+// [lo_bit, hi_bit), 8 bits per pass; alt is scratch of N keys; *sorted is
+// whichever of the two buffers holds the result.  Synchronises s.
+int radix_sort_u64(uint64_t* keys, uint64_t* alt, long long N, int lo_bit, int hi_bit, cudaStream_t s,
+                   uint64_t** sorted);
+// Exclusive prefix sum of N uint32 values into int64 out; *total receives the sum.
+int exclusive_scan_u32(const uint32_t* in, long long N, int64_t* out, cudaStream_t s, long long* total);
+// The 2D tiles of g's in-adjacency (see TileSet) with 2^rb_bits rows and
+// 2^cb_bits columns per tile (0: the defaults); synchronises s.
+int default_tile_rb_bits(int32_t n, int sm_count);
+int build_tiles(const bfs_graph* g, int sm_count, int rb_bits, int cb_bits, cudaStream_t s, TileSet** out);
+// g's tiles, built with the default layout if g has none (under g's lock).
+int ensure_tiles(bfs_graph* g, cudaStream_t s, TileSet** out);
+void free_tiles(TileSet* t);
 // Message of a nonzero device status (status[0] code, [1] site, [2..3] index).
 std::string device_status_message(const int* status4);
 // Row offsets non-decreasing from 0 to nnz?  d_flag: one device int of scratch.
@@ -169,6 +215,8 @@ struct RunRequest {
   unsigned spin_limit = 0;
   // ragged: scatter union outputs into per-part outputs (device table of 2*parts pointers)
   int32_t** part_out = nullptr;
+  // the graph's 2D tiles when a level may take the tiled variant (else the variant runs untiled)
+  const TileSet* tiles = nullptr;
 };
 // The grid barrier of kernel `kind` (0: level loop, 1: batched) in w, zeroed
 // on the stream first when that kernel's grid size differs from its last launch.

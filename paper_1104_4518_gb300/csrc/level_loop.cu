@@ -37,6 +37,7 @@
 #include <cooperative_groups/scan.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cstdio>
 
 #include "device_common.cuh"
@@ -118,6 +119,14 @@ struct LoopParams {
   int32_t parts;
   const int64_t* part_base;
   int32_t** part_out;  // [2 * parts]: level outputs then parent outputs
+  // 2D tiles of the in-adjacency for the tiled variant (t_jc null when absent)
+  const uint16_t* __restrict__ t_jc;
+  const uint32_t* __restrict__ t_cp;
+  const uint16_t* __restrict__ t_ir;
+  const int64_t* __restrict__ t_dir_jc;
+  const int64_t* __restrict__ t_dir_ir;
+  int32_t t_rb_bits, t_cb_bits, t_nrb, t_ncb;
+  int32_t tile_smem_off;  // byte offset of the tiled phase's slices in dynamic shared memory
 };
 
 // Per-thread accumulation of the next frontier's counters.
@@ -559,6 +568,133 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
   warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
 }
 
+// ---------------- tiled phase ----------------
+// Dense-frontier SpMV over the 2D tiles of the in-adjacency (Sec. 3.2's 2D
+// blocks, each in the DCSC form of Sec. 4.1).  A CTA owns a row block at a
+// time and keeps two tile-local slices in shared memory: `done`, the row
+// block's reached rows (vis | cur at level start, plus the rows found in the
+// tiles already walked), and `slice`, the frontier bits of the current column
+// block.  It walks the row block's tiles from the highest column block down;
+// in each tile the non-empty columns that are in the frontier expand their
+// rows (flattened over the CTA by a prefix sum, like the thread bin of the
+// top-down phase), and every row not yet done takes the column as a parent
+// candidate with atomicMax.  A row's candidates all come from the first tile
+// (in that order) that holds a frontier neighbour, since `done` only changes
+// between tiles, so the largest candidate is its max-id parent.  The row
+// block's found rows then go out as in the pull: owner-written nxt / vis
+// words, levels, counters and the warp queue buffers.
+constexpr int kTileWordsMax = 2048;  // 2^16 rows or columns per tile
+
+__device__ void tiled_phase(const LoopParams& p, int k, Smem& sm, uint32_t* tsm, Acc& acc) {
+  const uint32_t* cur = p.bits[k % 3];
+  uint32_t* nxt = p.bits[(k + 1) % 3];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int knext = k + 1;
+  uint32_t* done = tsm;
+  uint32_t* newf = tsm + kTileWordsMax;
+  uint32_t* slice = tsm + 2 * kTileWordsMax;
+  const int rbw = 1 << (p.t_rb_bits - 5), cbw = 1 << (p.t_cb_bits - 5);
+  int* wq = sm.cl.wq[wid];
+  int nbuf = 0;
+  for (int rb = blockIdx.x; rb < p.t_nrb; rb += gridDim.x) {
+    const long long w0 = (long long)rb * rbw;
+    bool live = false;
+    for (int i = tid; i < rbw; i += kBlock) {
+      const long long w = w0 + i;
+      const uint32_t d = w < p.nwords ? (p.vis[w] | cur[w]) : 0xffffffffu;
+      done[i] = d;
+      newf[i] = 0u;
+      live |= d != 0xffffffffu;
+    }
+    // a block whose rows are all reached walks no tile, but still folds cur into vis below
+    const int first_cb = __syncthreads_or(live) ? p.t_ncb - 1 : -1;
+    for (int cb = first_cb; cb >= 0; --cb) {
+      const long long t = (long long)rb * p.t_ncb + cb;
+      const long long j0 = p.t_dir_jc[t], j1 = p.t_dir_jc[t + 1];
+      if (j0 == j1) continue;  // empty tile (the same on every thread)
+      const long long ibase = p.t_dir_ir[t], iend = p.t_dir_ir[t + 1];
+      const long long s0 = (long long)cb * cbw;
+      for (int i = tid; i < cbw; i += kBlock) slice[i] = s0 + i < p.nwords ? cur[s0 + i] : 0u;
+      __syncthreads();
+      bool tile_hit = false;
+      for (long long jb = j0; jb < j1; jb += kBlock) {
+        const long long j = jb + tid;
+        int ul = -1;
+        long long rbeg = 0, rlen = 0;
+        if (j < j1) {
+          const int c = p.t_jc[j];
+          if ((slice[c >> 5] >> (c & 31)) & 1u) {
+            ul = c;
+            rbeg = ibase + p.t_cp[j];
+            rlen = (j + 1 < j1 ? ibase + p.t_cp[j + 1] : iend) - rbeg;
+          }
+        }
+        int excl = 0;
+        const int total = block_exclusive_scan((int)rlen, sm.warp_tmp, excl);
+        sm.tu[tid] = ul;
+        sm.tb[tid] = rbeg;
+        sm.tpref[tid] = excl;
+        if (tid == 0) sm.tpref[kBlock] = total;
+        __syncthreads();
+        for (int base = 0; base < total; base += kBlock) {
+          const int idx = base + tid;
+          if (idx < total) {
+            int lo = 0, hi = kBlock;  // largest slot with tpref <= idx (a frontier column with rows)
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (sm.tpref[mid] <= idx) lo = mid;
+              else hi = mid;
+            }
+            const int r = p.t_ir[sm.tb[lo] + (idx - sm.tpref[lo])];
+            if (!((done[r >> 5] >> (r & 31)) & 1u)) {
+              atomicMax(&p.parent[(rb << p.t_rb_bits) + r], (cb << p.t_cb_bits) + sm.tu[lo]);
+              atomicOr(&newf[r >> 5], 1u << (r & 31));
+              tile_hit = true;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      // the tile's rows are done from here on; stop once every row of the block is
+      if (__syncthreads_or(tile_hit)) {
+        live = false;
+        for (int i = tid; i < rbw; i += kBlock) {
+          const uint32_t d = done[i] | newf[i];
+          done[i] = d;
+          newf[i] = 0u;
+          live |= d != 0xffffffffu;
+        }
+        if (!__syncthreads_or(live)) break;
+      }
+    }
+    // rows found in this row block: done now minus reached at level start; every
+    // word of the block gets vis |= cur | found, as in the pull phase, so that
+    // f_k stays reached after its bitmap is recycled
+    for (int i = wid; i < rbw; i += kWarps) {
+      const long long w = w0 + i;
+      if (w >= p.nwords) break;
+      const uint32_t vw = p.vis[w], cw = cur[w];
+      const uint32_t visw = vw | cw;
+      const uint32_t f = done[i] & ~visw;
+      if (lane == 0) {
+        if (f) nxt[w] = f;
+        if ((visw | f) != vw) p.vis[w] = visw | f;
+      }
+      const bool hit = (f >> lane) & 1u;
+      const int v = (int)(w * 32 + lane);
+      if (hit) {
+        p.level[v] = knext;
+        const long long deg = __ldg(&p.off[v + 1]) - __ldg(&p.off[v]);
+        acc_vertex(acc, deg);
+        if (deg > p.chunk_deg) push_chunks_cta(p, knext, sm.cl, v, deg);
+      }
+      warp_enqueue(p, knext, wq, nbuf, hit, v, lane, false);
+    }
+    __syncthreads();
+  }
+  warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
+}
+
 // The selector network on one warp: every lane computes the 12 level features
 // in registers (lane j < 3 brings bin count j), then the warp evaluates the
 // network on the parameters in the warp layout; returns the chosen variant on
@@ -590,7 +726,12 @@ __device__ __forceinline__ int heuristic_variant(const LoopParams& p, int prev_v
 
 __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   __shared__ Smem sm;
-  extern __shared__ __align__(16) float s_mlp[];  // BFS_MLP_PARAMS floats when the learned selector is on
+  // dynamic shared memory: the selector network's parameters (BFS_MLP_PARAMS
+  // floats) when the learned selector is on, then the tiled phase's slices
+  // (3 * kTileWordsMax words) when tiles are present
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  float* s_mlp = reinterpret_cast<float*>(s_dyn);
+  uint32_t* s_tile = reinterpret_cast<uint32_t*>(s_dyn + p.tile_smem_off);
   const int tid = threadIdx.x;
   unsigned long long bar_target = 0;
   if (tid == 0) {
@@ -755,8 +896,10 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
       variant = heuristic_variant(p, prev_variant, count, prev_count, edges, unvisited_edges, big_rows == 0);
     }
     if (variant < 0 || variant >= BFS_NUM_VARIANTS) variant = BFS_VARIANT_TD_BINNED;
+    if (variant == BFS_VARIANT_TILED && p.t_jc == nullptr) variant = BFS_VARIANT_PULL;  // no tiles: the same SpMV untiled
     PHASE_TS(k, 2);
     if (variant == BFS_VARIANT_PULL) pull_phase(p, k, sm, acc);
+    else if (variant == BFS_VARIANT_TILED) tiled_phase(p, k, sm, s_tile, acc);
     else topdown_phase(p, k, variant, count, nchunks, sm, acc);
     PHASE_TS(k, 3);
     end_phase(p, k + 1, acc, sm);
@@ -842,6 +985,15 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   if (!g->d_off || !g->d_toff || (g->nnz > 0 && (!g->d_adj || !g->d_tadj)))
     return fail(BFS_ERR_INVALID_ARG, "graph without rows");
   const bfs_tuning t = effective_tuning(g);
+  // the tiled variant needs the graph's tiles: built here the first time a run may use it
+  bool may_tile = r.selector == BFS_SELECT_FORCED && r.forced == BFS_VARIANT_TILED;
+  for (int i = 0; i < sched_len && !may_tile; ++i) may_tile = r.h_schedule[i] == BFS_VARIANT_TILED;
+  const TileSet* tiles = r.tiles;
+  if (may_tile && tiles == nullptr) {
+    TileSet* ts = nullptr;
+    if (int e = ensure_tiles(g, s, &ts)) return e;
+    tiles = ts;
+  }
   LoopParams p{};
   p.off = g->d_off;
   p.adj = g->d_adj;
@@ -889,13 +1041,35 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   p.parts = g->parts;
   p.part_base = g->d_part_base;
   p.part_out = r.part_out;
+  if (may_tile && tiles != nullptr) {
+    const TileSet* ts = tiles;
+    p.t_jc = ts->jc;
+    p.t_cp = ts->cp;
+    p.t_ir = ts->ir;
+    p.t_dir_jc = ts->tdir_jc;
+    p.t_dir_ir = ts->tdir_ir;
+    p.t_rb_bits = ts->rb_bits;
+    p.t_cb_bits = ts->cb_bits;
+    p.t_nrb = ts->nrb;
+    p.t_ncb = ts->ncb;
+  }
 
-  const size_t dyn_smem = p.mlp ? sizeof(float) * BFS_MLP_PARAMS : 0;
-  static int configured = 0;
-  if (!configured) {
-    BFS_CUDA_TRY(cudaFuncSetAttribute(level_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(float) * BFS_MLP_PARAMS)));
-    configured = 1;
+  // the tiled variant's slices follow the network's parameters in dynamic shared memory
+  const size_t mlp_bytes = p.mlp ? (sizeof(float) * BFS_MLP_PARAMS + 15) / 16 * 16 : 0;
+  const size_t tile_bytes = p.t_jc ? sizeof(uint32_t) * 3 * kTileWordsMax : 0;
+  p.tile_smem_off = (int32_t)mlp_bytes;
+  const size_t dyn_smem = mlp_bytes + tile_bytes;
+  {  // the attribute belongs to the current device: set it once per device
+    static std::mutex mu;
+    static bool configured[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (di.device < 0 || di.device >= 64) return fail(BFS_ERR_UNSUPPORTED, "device ordinal out of range");
+    if (!configured[di.device]) {
+      BFS_CUDA_TRY(cudaFuncSetAttribute(level_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((sizeof(float) * BFS_MLP_PARAMS + 15) / 16 * 16 +
+                                              sizeof(uint32_t) * 3 * kTileWordsMax)));
+      configured[di.device] = true;
+    }
   }
   int per_sm = 0;
   BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_loop_kernel, kBlock, dyn_smem));

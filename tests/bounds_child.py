@@ -9,7 +9,8 @@ bounds-checking build: through the normal build those inputs would read and
 write outside the arrays.  Every bad id is planted where the traversal reads
 it on its first level (the last entry of a row, which keeps the row sorted):
 a row of the source for the top-down variants, a row of an unvisited vertex
-for the pull variant, whose first probe loads the last entries of a row.
+for the pull variant, whose first probe loads the last entries of a row; the
+tiled variant's tile builder reads every id and rejects the graph.
 Prints one line per case and exits non-zero on the first failure.
 """
 import os
@@ -158,7 +159,8 @@ def malformed():
     for name, adj_h, variants, site in (
             ("id n+5 in the source row", adj_td, range(3), "top-down adjacency id"),
             ("id -3 in the source row", adj_neg, range(3), "top-down adjacency id"),
-            ("id n+7 in an unvisited row", adj_pull, [bfs.BFS_VARIANT_PULL], "pull adjacency id")):
+            ("id n+7 in an unvisited row", adj_pull, [bfs.BFS_VARIANT_PULL], "pull adjacency id"),
+            ("id n+7 in an unvisited row", adj_pull, [bfs.BFS_VARIANT_TILED], "tile adjacency id")):
         g = bfs.bfs_graph_create(off, torch.from_numpy(adj_h).cuda())  # no BFS_VALIDATE
         for v in variants:
             o = bfs.RunOptions(selector=bfs.BFS_SELECT_FORCED, forced_variant=v)

@@ -78,6 +78,7 @@ def test_runs_reject_missing_graphs_and_bad_sources(lib):
     expect(lib, lib.bfs_get_tuning(None, None), INVALID_ARG, "NULL graph")
     expect(lib, lib.bfs_autotune(None, None, 0, None, None), INVALID_ARG, "NULL graph")
     expect(lib, lib.bfs_graph_info(None, None, None, None), INVALID_ARG, "NULL graph")
+    expect(lib, lib.bfs_graph_tiles(None, 0, 0, None, None), INVALID_ARG, "NULL graph")
 
 
 def test_static_entry_point_checks_before_any_device_work(lib):

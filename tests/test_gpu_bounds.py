@@ -47,5 +47,5 @@ def test_checked_build_is_bit_identical_on_well_formed_graphs():
 
 def test_checked_build_reports_bad_indices():
     out = run_child("malformed")
-    assert out.count("BFS_ERR_BOUNDS") == 3 + 3 + 1 + 2 + 2 + 2
+    assert out.count("BFS_ERR_BOUNDS") == 3 + 3 + 1 + 1 + 2 + 2 + 2  # + the tiled variant's tile builder
     assert "clean runs after the errors: ok" in out

@@ -135,6 +135,37 @@ def test_rmat26_forced_variants_schedules_and_learned_selector(rmat26):
     assert val.finish() == len(picks)
 
 
+def test_rmat26_learned_selector_beats_the_heuristic(rmat26):
+    """On the scale-26 benchmark graph, the 64 bench roots traversed with the learned
+    selector (shipped weights) take less device time than with the fixed-threshold
+    heuristic: alternating rounds, the median of three for each.  (The network
+    keeps pull one level longer where the heuristic's exit threshold leaves it
+    early, and runs the last levels thread-per-vertex.)"""
+    _, roots, g = rmat26
+    n = g.info()[0]
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    bfs.bfs_selector_load(WEIGHTS)
+    try:
+        times = {bfs.BFS_SELECT_HEURISTIC: [], bfs.BFS_SELECT_LEARNED: []}
+        for rnd in range(4):
+            for sel in times:
+                o = bfs.RunOptions(selector=sel)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for s in roots:
+                    bfs.bfs_run(g, s, parent, level, o)
+                e1.record()
+                torch.cuda.synchronize()
+                if rnd > 0:  # the first round warms up
+                    times[sel].append(e0.elapsed_time(e1))
+        heur, learned = (float(np.median(times[s])) for s in (bfs.BFS_SELECT_HEURISTIC, bfs.BFS_SELECT_LEARNED))
+        print(f"\nscale 26, 64 roots: heuristic {heur:.2f} ms, learned {learned:.2f} ms")
+        assert learned < heur, (learned, heur)
+    finally:
+        bfs.bfs_selector_set_params(None)
+
+
 def test_heldout_rmat25_learned_selector():
     """The selector's held-out R-MAT graph (scale 25, edgefactor 16, graph seed 7,
     8 roots of seed 107) traversed with the learned selector and the shipped weights:
@@ -228,3 +259,34 @@ def test_grid256_closed_form(selector):
     exp = np.where(x > 0, v - 1, np.where(y > 0, v - N, v - N * N))
     exp[0] = 0
     assert np.array_equal(parent, exp.astype(np.int32))
+
+
+@pytest.mark.parametrize("ef", [4, 8, 16, 32, 64])
+def test_degree_sweep_graphs_validated(ef):
+    """The graphs of the average-degree sweep (`paper_1104_4518_gb300.sweep`: R-MAT with
+    2^27 generated edges, edgefactor ef, scale 27 - log2 ef, graph seed 40 + ef, roots
+    seed 140 + ef): the first sweep root under the heuristic and the learned selector,
+    and the first two rows of the batched traversal of the sweep's 16 roots, validated
+    edge by edge against the oracle's rule."""
+    from paper_1104_4518_gb300 import sweep
+
+    scale = sweep.LOG2_EDGES - int(np.log2(ef))
+    el = inputs.rmat(scale, ef, seed=40 + ef)
+    roots = [int(r) for r in inputs.roots(el, 16, 140 + ef)]
+    g = device_graph_from_edges(el)
+    val = Validations(el)
+    bfs.bfs_selector_load(WEIGHTS)
+    try:
+        for sel in (bfs.BFS_SELECT_HEURISTIC, bfs.BFS_SELECT_LEARNED):
+            parent, level = bfs.run(g, roots[0], bfs.RunOptions(selector=sel))
+            bfs.bfs_sync(g)
+            val.submit(f"ef {ef} selector {sel}", roots[0], level, parent)
+        pb, lb = bfs.run_batch(g, roots)
+        bfs.bfs_sync(g)
+        for i in range(2):
+            val.submit(f"ef {ef} batched row {i}", roots[i], lb[i], pb[i])
+        del pb, lb
+    finally:
+        bfs.bfs_selector_set_params(None)
+        g.destroy()
+    assert val.finish() == 4
