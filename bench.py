@@ -534,6 +534,23 @@ def run_gpu(args, wl):
             var[name] = round(harmonic_gteps(e_one[:len(few)], list(ft.flatten() / 1e3)), 3)
         bfs.bfs_sync(g)
         comp["forced_variant_gteps_4_roots"] = var
+        # degree-binned expansion with the dense-frontier levels walked untiled (the heuristic's
+        # schedule) against the same schedule with those levels on the 2D DCSC tiles
+        sched = {}
+        for s in few:
+            so = bfs.RunOptions(stats_levels=256)
+            bfs.bfs_run(g, s, parent, level, so)
+            bfs.bfs_sync(g)
+            sched[s] = [bfs.BFS_VARIANT_TILED if x["variant"] == bfs.BFS_VARIANT_PULL else x["variant"]
+                        for x in so.stats()]
+        tt = timed_roots(lambda s: bfs.bfs_run(g, s, parent, level, bfs.RunOptions(
+            selector=bfs.BFS_SELECT_SCHEDULE, schedule=sched[s])), few, 1, 1, stream)
+        ht = timed_roots(lambda s: bfs.bfs_run(g, s, parent, level), few, 1, 1, stream)
+        comp["binned_with_pull_vs_tiled_4_roots"] = {
+            "untiled_gteps": round(harmonic_gteps(e_one[:len(few)], list(ht.flatten() / 1e3)), 3),
+            "tiled_gteps": round(harmonic_gteps(e_one[:len(few)], list(tt.flatten() / 1e3)), 3),
+            "how": "the heuristic's per-level schedule (degree-binned / warp top-down levels, dense-frontier "
+                   "levels) replayed with the dense-frontier levels on the 2D DCSC tiles"}
         # autotuned: tuning picked on 8 other seeded roots, then all timed roots
         if wl["kind"] == "rmat":
             tune_roots = inputs.roots(el, 8, wl["root_seed"] + 7777)

@@ -724,6 +724,10 @@ __device__ __forceinline__ int heuristic_variant(const LoopParams& p, int prev_v
   return (count <= p.small_frontier && small_rows) ? BFS_VARIANT_TD_WARP : BFS_VARIANT_TD_BINNED;
 }
 
+// kTiles: the kernel can run the tiled phase.  Runs that cannot pick the tiled
+// variant launch the instance without it: on R-MAT scale 26 the tiled phase's
+// code alone made the other phases 5 % slower.
+template <bool kTiles>
 __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   __shared__ Smem sm;
   // dynamic shared memory: the selector network's parameters (BFS_MLP_PARAMS
@@ -896,10 +900,10 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
       variant = heuristic_variant(p, prev_variant, count, prev_count, edges, unvisited_edges, big_rows == 0);
     }
     if (variant < 0 || variant >= BFS_NUM_VARIANTS) variant = BFS_VARIANT_TD_BINNED;
-    if (variant == BFS_VARIANT_TILED && p.t_jc == nullptr) variant = BFS_VARIANT_PULL;  // no tiles: the same SpMV untiled
+    if (variant == BFS_VARIANT_TILED && (!kTiles || p.t_jc == nullptr)) variant = BFS_VARIANT_PULL;  // the SpMV untiled
     PHASE_TS(k, 2);
     if (variant == BFS_VARIANT_PULL) pull_phase(p, k, sm, acc);
-    else if (variant == BFS_VARIANT_TILED) tiled_phase(p, k, sm, s_tile, acc);
+    else if (kTiles && variant == BFS_VARIANT_TILED) tiled_phase(p, k, sm, s_tile, acc);
     else topdown_phase(p, k, variant, count, nchunks, sm, acc);
     PHASE_TS(k, 3);
     end_phase(p, k + 1, acc, sm);
@@ -1059,20 +1063,23 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   const size_t tile_bytes = p.t_jc ? sizeof(uint32_t) * 3 * kTileWordsMax : 0;
   p.tile_smem_off = (int32_t)mlp_bytes;
   const size_t dyn_smem = mlp_bytes + tile_bytes;
+  const void* kernel = p.t_jc ? (const void*)level_loop_kernel<true> : (const void*)level_loop_kernel<false>;
   {  // the attribute belongs to the current device: set it once per device
     static std::mutex mu;
     static bool configured[64] = {};
     std::lock_guard<std::mutex> lk(mu);
     if (di.device < 0 || di.device >= 64) return fail(BFS_ERR_UNSUPPORTED, "device ordinal out of range");
     if (!configured[di.device]) {
-      BFS_CUDA_TRY(cudaFuncSetAttribute(level_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)((sizeof(float) * BFS_MLP_PARAMS + 15) / 16 * 16 +
-                                              sizeof(uint32_t) * 3 * kTileWordsMax)));
+      const int max_dyn = (int)((sizeof(float) * BFS_MLP_PARAMS + 15) / 16 * 16 + sizeof(uint32_t) * 3 * kTileWordsMax);
+      BFS_CUDA_TRY(cudaFuncSetAttribute((const void*)level_loop_kernel<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
+      BFS_CUDA_TRY(cudaFuncSetAttribute((const void*)level_loop_kernel<true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
       configured[di.device] = true;
     }
   }
   int per_sm = 0;
-  BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_loop_kernel, kBlock, dyn_smem));
+  BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, dyn_smem));
   if (per_sm < 1) return fail(BFS_ERR_CUDA, "level loop kernel cannot be resident");
   const int grid = per_sm * di.sm_count;
   if (int e = prepare_barrier(w, 0, grid, s, &p.bar)) return e;
@@ -1081,8 +1088,7 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   fprintf(stderr, "level loop: %d CTAs (%d per SM), %zu bytes dynamic shared memory\n", grid, per_sm, dyn_smem);
 #endif
   void* args[] = {&p};
-  BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)level_loop_kernel, dim3(grid), dim3(kBlock), args,
-                                           dyn_smem, s));
+  BFS_CUDA_TRY(cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kBlock), args, dyn_smem, s));
   return BFS_OK;
 }
 
