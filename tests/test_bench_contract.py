@@ -46,7 +46,7 @@ def test_harmonic_mean_of_rates():
 
 
 def test_profile_traffic_counts_only_for_the_recorded_kernel_source(monkeypatch):
-    name = "level_loop_rmat22.md"
+    name = "level_loop_rmat23.md"
     text = open(os.path.join(ROOT, "profiles", name)).read()
     recorded = [ln.split("`")[1] for ln in text.splitlines() if ln.startswith("- source_sha256:")][0]
     traffic = float([ln.split(":")[1] for ln in text.splitlines() if ln.startswith("- traffic_bytes_per_launch:")][0])
@@ -69,3 +69,18 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_traffic_of_a_larger_workload_is_scaled_from_the_small_capture(monkeypatch):
+    """A workload without its own capture takes the scale-23 capture's traffic times the
+    ratio of algorithmic bytes per launch; a stale capture gives no traffic."""
+    kv = bench.profile_summary(bench.SCALED_CAPTURE)
+    t23, a23 = float(kv["traffic_bytes_per_launch"]), float(kv["algorithmic_bytes_per_launch"])
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: kv["source_sha256"])
+    t, how = bench.traffic_estimate("rmat26", 8 * a23)
+    assert t == pytest.approx(8 * t23) and "scaled" in how
+    t, how = bench.traffic_estimate("rmat23", a23)
+    assert t == pytest.approx(t23) and "this workload" in how
+    assert bench.traffic_estimate("grid128", 1e9)[0] is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.traffic_estimate("rmat26", 8 * a23)[0] is None
