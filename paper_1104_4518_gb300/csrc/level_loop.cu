@@ -412,6 +412,8 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
 }
 
 // ---------------- pull phase ----------------
+constexpr int kPullRows = 2;    // live rows per lane in flight
+constexpr int kPullProbes = 4;  // at most this many top entries of each row are probed before the warp scan
 // Position of the r-th (0-based) set bit of m; r < popc(m).
 __device__ __forceinline__ int select_bit(uint32_t m, int r) {
   int pos = 0;
@@ -447,48 +449,51 @@ __device__ __forceinline__ int live_vertex(long long chunk, uint32_t live, int i
   return (int)((chunk * 32 + o) * 32 + b);
 }
 
-// The max-id frontier neighbour of one row per lane (v < 0: no row), for two
-// rows per lane at once: row bounds, a probe of the top `probe` entries of
-// each row with their frontier words in flight together, then the warp's
-// cooperative descending scan of the rows still open.
-__device__ __forceinline__ void pull_rows2(const LoopParams& p, const uint32_t* cur, int probe, int lane, int va,
-                                           int vb, int& ha, int& hb, long long& ea, long long& da, long long& eb,
-                                           long long& db) {
-  long long ba = 0, bb = 0;
-  ea = eb = 0;
-  if (va >= 0) {
-    ba = __ldg(&p.toff[va]);
-    ea = __ldg(&p.toff[va + 1]);
-  }
-  if (vb >= 0) {
-    bb = __ldg(&p.toff[vb]);
-    eb = __ldg(&p.toff[vb + 1]);
-  }
-  const int PA = va >= 0 ? (int)min((long long)probe, ea - ba) : 0;
-  const int PB = vb >= 0 ? (int)min((long long)probe, eb - bb) : 0;
-  int ua[4], ub[4];
-  uint32_t xa[4], xb[4];
+// The max-id frontier neighbour of R rows per lane (v[r] < 0: no row): the
+// rows' bounds, then a probe of the top `probe` (<= P) entries of every row with all their
+// adjacency loads and then all their frontier-word loads in flight together,
+// then the warp's cooperative descending scan of the rows still open.  R = 2,
+// P = 4 is what the 64-register budget holds without spills (R = 3 or 4 with
+// P = 2 spilled and ran 5 % and 16 % slower on R-MAT scale 26).
+template <int R, int P>
+__device__ __forceinline__ void pull_rows(const LoopParams& p, const uint32_t* cur, int lane, int probe,
+                                          const int (&v)[R], int (&h)[R], long long (&d)[R]) {
+  long long b[R], e[R];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    ua[q] = q < PA ? __ldg(&p.tadj[ea - 1 - q]) : 0;
-    ub[q] = q < PB ? __ldg(&p.tadj[eb - 1 - q]) : 0;
+  for (int r = 0; r < R; ++r) {
+    b[r] = e[r] = 0;
+    if (v[r] >= 0) {
+      b[r] = __ldg(&p.toff[v[r]]);
+      e[r] = __ldg(&p.toff[v[r] + 1]);
+    }
+  }
+  int np[R];
+  int u[R][P];
+  uint32_t x[R][P];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    np[r] = v[r] >= 0 ? (int)min((long long)probe, e[r] - b[r]) : 0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) u[r][q] = q < np[r] ? __ldg(&p.tadj[e[r] - 1 - q]) : 0;
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    xa[q] = q < PA && bfsdev::in_range(p.status, bfsdev::kSitePull, ua[q], p.n) ? cur[ua[q] >> 5] : 0u;
-    xb[q] = q < PB && bfsdev::in_range(p.status, bfsdev::kSitePull, ub[q], p.n) ? cur[ub[q] >> 5] : 0u;
-  }
-  ha = hb = -1;
+  for (int r = 0; r < R; ++r)
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (q < PA && ha < 0 && ((xa[q] >> (ua[q] & 31)) & 1u)) ha = ua[q];
-    if (q < PB && hb < 0 && ((xb[q] >> (ub[q] & 31)) & 1u)) hb = ub[q];
+    for (int q = 0; q < P; ++q)
+      x[r][q] = q < np[r] && bfsdev::in_range(p.status, bfsdev::kSitePull, u[r][q], p.n) ? cur[u[r][q] >> 5] : 0u;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    h[r] = -1;
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+      if (q < np[r] && h[r] < 0 && ((x[r][q] >> (u[r][q] & 31)) & 1u)) h[r] = u[r][q];
   }
-  const long long ta = ea - PA, tb = eb - PB;
-  ha = scan_desc_coop(p.tadj, cur, ba, ta, va >= 0 && ha < 0 && ta > ba, ha, lane, p.status, p.n);
-  hb = scan_desc_coop(p.tadj, cur, bb, tb, vb >= 0 && hb < 0 && tb > bb, hb, lane, p.status, p.n);
-  da = ea - ba;
-  db = eb - bb;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long t = e[r] - np[r];
+    h[r] = scan_desc_coop(p.tadj, cur, b[r], t, v[r] >= 0 && h[r] < 0 && t > b[r], h[r], lane, p.status, p.n);
+    d[r] = e[r] - b[r];
+  }
 }
 
 // Bookkeeping of a vertex v reached by the pull (hit = its parent): outputs,
@@ -522,7 +527,7 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long gwarps = (long long)gridDim.x * kWarps;
   const int knext = k + 1;
-  const int probe = min(p.pull_thread_deg, 4);
+  const int probe = min(p.pull_thread_deg, kPullProbes);  // the tuning knob, at most kPullProbes
   int* wq = sm.cl.wq[wid];
   uint32_t* hitw = sm.pull_hits[wid];
   int nbuf = 0;
@@ -544,18 +549,20 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
     const int total = __shfl_sync(kFull, incl, 31);
     hitw[lane] = 0u;
     __syncwarp();
-    for (int base = 0; base < total; base += 64) {
-      int oa, ob;
-      uint32_t bita, bitb;
-      const int ia = base + lane, ib = base + 32 + lane;
-      const int la = live_vertex(c, live, incl, min(ia, total - 1), oa, bita);
-      const int lb = live_vertex(c, live, incl, min(ib, total - 1), ob, bitb);
-      const int va = ia < total ? la : -1, vb = ib < total ? lb : -1;
-      int ha, hb;
-      long long ea, da, eb, db;
-      pull_rows2(p, cur, probe, lane, va, vb, ha, hb, ea, da, eb, db);
-      pull_claim(p, knext, va, va >= 0 ? ha : -1, da, hitw, oa, bita, acc, sm.cl, wq, nbuf, lane);
-      pull_claim(p, knext, vb, vb >= 0 ? hb : -1, db, hitw, ob, bitb, acc, sm.cl, wq, nbuf, lane);
+    for (int base = 0; base < total; base += 32 * kPullRows) {
+      int v[kPullRows], o[kPullRows], h[kPullRows];
+      uint32_t bit[kPullRows];
+      long long d[kPullRows];
+#pragma unroll
+      for (int r = 0; r < kPullRows; ++r) {
+        const int i = base + r * 32 + lane;
+        const int lv = live_vertex(c, live, incl, min(i, total - 1), o[r], bit[r]);
+        v[r] = i < total ? lv : -1;
+      }
+      pull_rows<kPullRows, kPullProbes>(p, cur, lane, probe, v, h, d);
+#pragma unroll
+      for (int r = 0; r < kPullRows; ++r)
+        pull_claim(p, knext, v[r], v[r] >= 0 ? h[r] : -1, d[r], hitw, o[r], bit[r], acc, sm.cl, wq, nbuf, lane);
     }
     __syncwarp();
     const uint32_t hits = hitw[lane];

@@ -33,6 +33,10 @@ int main(int argc, char** argv) {
                BFS_ERR_INVALID_ARG);
   bad |= check("bfs_run_static with a source outside [0, n)",
                bfs_run_static(off, adj, 2, 2, 7, buf, buf, NULL), BFS_ERR_INVALID_ARG);
+  {
+    bfs_tile_info info;
+    bad |= check("bfs_graph_tiles without a graph", bfs_graph_tiles(NULL, 0, 0, &info, NULL), BFS_ERR_INVALID_ARG);
+  }
   if (g != NULL) {
     fprintf(stderr, "a failed create left a graph behind\n");
     bad = 1;
