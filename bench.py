@@ -560,7 +560,7 @@ def run_gpu(args, wl):
             comp["autotuned"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuned.as_dict().items()}
             bfs.bfs_set_tuning(g, **{f: 0 for f in ("warp_degree", "cta_degree", "pull_thread_degree",
                                                      "chunk_degree", "batch_topdown_limit", "small_frontier",
-                                                     "batch_width")}, alpha=0.0, beta=0.0)
+                                                     "batch_width", "narrow_edges")}, alpha=0.0, beta=0.0)
         # the batched configuration's own graph (R-MAT scale 24, graph seed 4 / roots 104): 64 roots in
         # one batched traversal against 64 single-root traversals of the same roots
         if wl["kind"] == "rmat" and wl["scale"] != 24 and not args.no_batched_config:

@@ -126,7 +126,9 @@ typedef struct bfs_tuning {
                              in the traversal's grid; negative = never) */
   int32_t batch_width;   /* batched: roots per traversal, the bits of a frontier word: 8, 16, 32 or 64
                             (default 64) */
-  int32_t reserved;
+  int32_t narrow_edges;  /* a level whose frontier has at most this many edges runs on half the CTAs of the
+                            traversal's grid, which also halves its barrier's arrivals (0 = default 16384;
+                            negative = never) */
 } bfs_tuning;
 
 /* Options of one run (NULL = heuristic selector, no statistics). */

@@ -131,6 +131,48 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned nblocks,
   return s_ok != 0;
 }
 
+// The grid barrier of a level that only `arrivals` CTAs (those with
+// blockIdx.x < arrivals) worked on: those CTAs arrive as in grid_barrier, the
+// others only wait until the counter reaches the new target (polling less
+// often, since nothing waits on them).  Every CTA must pass the same
+// `arrivals`.  A launch that used such barriers must pad the counter to a
+// multiple of its grid size before it ends (barrier_pad).
+__device__ __forceinline__ bool grid_barrier_partial(GridBarrier* bar, unsigned arrivals, unsigned long long& target,
+                                                     unsigned spin_limit, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const bool arrive = blockIdx.x < arrivals;
+    target += arrivals;
+    if (arrive) {
+      __threadfence();
+      red_release_add_u64(&bar->count, 1ull);
+    }
+    unsigned polls = 0;
+    while (ld_acquire_u64(&bar->count) < target) {
+      if (++polls > spin_limit || ld_relaxed_i32(status) != 0) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(arrive ? 32 : 256);
+    }
+    if (!ok) atomicCAS(status, 0, (int)BFS_ERR_TIMEOUT);
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Called by one thread of one CTA after the last barrier of a launch: adds
+// the arrivals that round the counter up to a multiple of nblocks, so that
+// the next launch's barrier_base finds its base.  `target` is that thread's
+// copy of the last barrier's target.
+__device__ __forceinline__ void barrier_pad(GridBarrier* bar, unsigned nblocks, unsigned long long target) {
+  const unsigned long long r = target % nblocks;
+  if (r) red_release_add_u64(&bar->count, nblocks - r);
+}
+
 // The count at which this launch's barriers start, read by thread 0 at kernel
 // start.  Every launch that used the word before ended on a multiple of
 // nblocks (the host zeroes the word when a kernel's grid size changes, and

@@ -116,6 +116,7 @@ struct LoopParams {
   int32_t warp_deg, cta_deg, pull_thread_deg, chunk_deg;
   float alpha, beta;
   long long small_frontier;  // TD_WARP for top-down levels up to this many vertices, all of degree <= 32
+  long long narrow_edges;    // levels whose frontier has at most this many edges run on half the CTAs
   int32_t parts;
   const int64_t* part_base;
   int32_t** part_out;  // [2 * parts]: level outputs then parent outputs
@@ -300,7 +301,7 @@ struct Smem {
 
 // ---------------- top-down phase ----------------
 __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned count, unsigned nchunks, Smem& sm,
-                              Acc& acc) {
+                              Acc& acc, unsigned G) {
   const uint32_t* cur = p.bits[k % 3];
   uint32_t* nxt = p.bits[(k + 1) % 3];
   const int32_t* Q = p.queue[k % 3];
@@ -309,7 +310,7 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
   // chunk items of high-degree frontier vertices: one CTA per item; before each
   // item the CTA makes room in its buffers for the item's claims
   const int64_t* items = p.chunks[k & 1];
-  for (unsigned ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+  for (unsigned ci = blockIdx.x; ci < nchunks; ci += G) {
     flush_claims_if_full(p, k + 1, sm.cl, kChunkEdges, kBigBuf / 2);
     const int64_t it = items[ci];
     const int v = (int)(it >> 32);
@@ -320,9 +321,8 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
     for (long long j = b + tid; j < e; j += kBlock) td_visit(p, cur, nxt, k, v, __ldg(&p.adj[j]), acc, sm.cl);
   }
 
-  // frontier entry i goes to CTA i % G, so that small frontiers spread over every SM
-  const long long G = gridDim.x;
-  const long long gthreads = G * kBlock;
+  // frontier entry i goes to CTA i % G, so that small frontiers spread over the SMs
+  const long long gthreads = (long long)G * kBlock;
   if (variant == BFS_VARIANT_TD_THREAD) {
     for (long long i = blockIdx.x + (long long)tid * G; i < count; i += gthreads) {
       const int u = Q[i];
@@ -521,18 +521,18 @@ __device__ __forceinline__ void pull_claim(const LoopParams& p, int knext, int v
 // scale-26 R-MAT graph most words hold one live vertex).  Each word's hits are
 // gathered in shared memory and its owner lane writes the word's `nxt` and
 // `vis` (no global atomics on the bitmaps).
-__device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
+__device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc, unsigned G) {
   const uint32_t* cur = p.bits[k % 3];
   uint32_t* nxt = p.bits[(k + 1) % 3];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long gwarps = (long long)gridDim.x * kWarps;
+  const long long gwarps = (long long)G * kWarps;
   const int knext = k + 1;
   const int probe = min(p.pull_thread_deg, kPullProbes);  // the tuning knob, at most kPullProbes
   int* wq = sm.cl.wq[wid];
   uint32_t* hitw = sm.pull_hits[wid];
   int nbuf = 0;
   const long long nchunks = ((long long)p.nwords + 31) / 32;
-  for (long long c = (long long)wid * gridDim.x + blockIdx.x; c < nchunks; c += gwarps) {
+  for (long long c = (long long)wid * G + blockIdx.x; c < nchunks; c += gwarps) {
     const long long w = c * 32 + lane;
     const bool has = w < p.nwords;
     const uint32_t vw = has ? p.vis[w] : 0xffffffffu;
@@ -592,7 +592,7 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc) {
 // words, levels, counters and the warp queue buffers.
 constexpr int kTileWordsMax = 2048;  // 2^16 rows or columns per tile
 
-__device__ void tiled_phase(const LoopParams& p, int k, Smem& sm, uint32_t* tsm, Acc& acc) {
+__device__ void tiled_phase(const LoopParams& p, int k, Smem& sm, uint32_t* tsm, Acc& acc, unsigned G) {
   const uint32_t* cur = p.bits[k % 3];
   uint32_t* nxt = p.bits[(k + 1) % 3];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -603,7 +603,7 @@ __device__ void tiled_phase(const LoopParams& p, int k, Smem& sm, uint32_t* tsm,
   const int rbw = 1 << (p.t_rb_bits - 5), cbw = 1 << (p.t_cb_bits - 5);
   int* wq = sm.cl.wq[wid];
   int nbuf = 0;
-  for (int rb = blockIdx.x; rb < p.t_nrb; rb += gridDim.x) {
+  for (int rb = blockIdx.x; rb < p.t_nrb; rb += G) {
     const long long w0 = (long long)rb * rbw;
     bool live = false;
     for (int i = tid; i < rbw; i += kBlock) {
@@ -875,17 +875,26 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
     const long long unvisited = (long long)p.n - cum_count;
     const long long unvisited_edges = p.nnz - cum_edges;
 
+    // A level whose frontier has few edges runs on the first half of the CTAs
+    // (one per SM when two are resident): only they recycle, expand and arrive
+    // at its barrier, which halves the barrier's arrivals and the CTAs that
+    // contend for the level's few claims.  The other CTAs still choose the
+    // variant (the next level's choice depends on it) and wait at the barrier.
+    const unsigned G = (edges <= p.narrow_edges && nblocks >= 2) ? (nblocks + 1) / 2 : nblocks;
+    const bool part = blockIdx.x < G;
+    const long long pthreads = (long long)G * kBlock;
+
     // recycle: counters of level k+4, bitmap of level k-1 (stores only; they
     // drain while the selector runs)
     if (blockIdx.x == 0 && tid < (int)(sizeof(LevelCtr) / 8))
       reinterpret_cast<unsigned long long*>(&p.ctr[(k + 4) % kCtrRing])[tid] = 0ull;
-    if (k >= 1) {
+    if (k >= 1 && part) {
       uint32_t* clr = p.bits[(k + 2) % 3];
       if (sparse_clr) {
         if (clr0 >= 0) clr[clr0 >> 5] = 0u;
-        for (long long i = gtid + gthreads; i < prev_count; i += gthreads) clr[PQ[i] >> 5] = 0u;
+        for (long long i = gtid + pthreads; i < prev_count; i += pthreads) clr[PQ[i] >> 5] = 0u;
       } else {
-        for (long long w = gtid; w < p.nwords; w += gthreads) clr[w] = 0u;
+        for (long long w = gtid; w < p.nwords; w += pthreads) clr[w] = 0u;
       }
     }
     PHASE_TS(k, 1);
@@ -909,14 +918,16 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
     if (variant < 0 || variant >= BFS_NUM_VARIANTS) variant = BFS_VARIANT_TD_BINNED;
     if (variant == BFS_VARIANT_TILED && (!kTiles || p.t_jc == nullptr)) variant = BFS_VARIANT_PULL;  // the SpMV untiled
     PHASE_TS(k, 2);
-    if (variant == BFS_VARIANT_PULL) pull_phase(p, k, sm, acc);
-    else if (kTiles && variant == BFS_VARIANT_TILED) tiled_phase(p, k, sm, s_tile, acc);
-    else topdown_phase(p, k, variant, count, nchunks, sm, acc);
-    PHASE_TS(k, 3);
-    end_phase(p, k + 1, acc, sm);
+    if (part) {
+      if (variant == BFS_VARIANT_PULL) pull_phase(p, k, sm, acc, G);
+      else if (kTiles && variant == BFS_VARIANT_TILED) tiled_phase(p, k, sm, s_tile, acc, G);
+      else topdown_phase(p, k, variant, count, nchunks, sm, acc, G);
+      PHASE_TS(k, 3);
+      end_phase(p, k + 1, acc, sm);
+    }
     PHASE_TS(k, 4);
     PHASE_ARRIVAL(k);
-    if (!bfsdev::grid_barrier(p.bar, nblocks, bar_target, p.spin_limit, p.status)) return;
+    if (!bfsdev::grid_barrier_partial(p.bar, G, bar_target, p.spin_limit, p.status)) return;
     PHASE_TS(k, 6);
 
     if (p.want_stats && blockIdx.x == 0 && tid == 0 && k < kMaxStatLevels) {
@@ -940,6 +951,7 @@ __global__ void __launch_bounds__(kBlock, 2) level_loop_kernel(LoopParams p) {
   }
 
   if (gtid == 0) {
+    bfsdev::barrier_pad(p.bar, nblocks, bar_target);  // partial barriers: round the counter to the grid size
     p.misc[0] = k;
     *p.edges_out = p.directed ? cum_edges : cum_edges / 2;  // arcs, or undirected edges
   }
@@ -1091,6 +1103,7 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   const int grid = per_sm * di.sm_count;
   if (int e = prepare_barrier(w, 0, grid, s, &p.bar)) return e;
   p.small_frontier = t.small_frontier > 0 ? t.small_frontier : (t.small_frontier == 0 ? (long long)grid * kWarps : 0);
+  p.narrow_edges = t.narrow_edges > 0 ? t.narrow_edges : (t.narrow_edges == 0 ? (1ll << 14) : -1);
 #ifdef BFS_PHASE_TIMING
   fprintf(stderr, "level loop: %d CTAs (%d per SM), %zu bytes dynamic shared memory\n", grid, per_sm, dyn_smem);
 #endif
