@@ -335,7 +335,7 @@ BFS_API int bfs_get_tuning(const bfs_graph* g, bfs_tuning* t);
 /*
  * Times bfs_run over `nroots` host roots (ids) for a small grid of tuning
  * candidates (bin degrees, pull thread degree, chunk degree, heuristic alpha,
- * beta and small_frontier; coordinate descent, two sweeps), then
+ * beta, small_frontier and narrow_edges; coordinate descent, two sweeps), then
  * bfs_run_batch over the first 64 of them for the batched top-down limit; keeps
  * the fastest as the graph's tuning and copies it to *best.
  * Synchronises the stream; results never change, only speed.

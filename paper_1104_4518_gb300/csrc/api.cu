@@ -910,8 +910,9 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
     const float al[] = {10.0f, 14.0f, 20.0f, 30.0f, 45.0f};
     const float be[] = {8.0f, 16.0f, 24.0f, 48.0f, 96.0f};
     const int sf[] = {-1, 0, 2 * 4864, 4 * 4864};
-    for (int knob = 0; knob < 7 && !rc; ++knob) {
-      const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 3 : knob == 6 ? 4 : 5;
+    const int ne[] = {-1, 4096, 16384, 65536};
+    for (int knob = 0; knob < 8 && !rc; ++knob) {
+      const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 3 : knob >= 6 ? 4 : 5;
       for (int c = 0; c < cnt && !rc; ++c) {
         bfs_tuning t = cur;
         switch (knob) {
@@ -921,7 +922,8 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
           case 3: t.chunk_degree = ch[c]; break;
           case 4: t.alpha = al[c]; break;
           case 5: t.beta = be[c]; break;
-          default: t.small_frontier = sf[c]; break;
+          case 6: t.small_frontier = sf[c]; break;
+          default: t.narrow_edges = ne[c]; break;
         }
         float ms = 0.0f;
         rc = time_plain(t, &ms);

@@ -155,7 +155,7 @@ __device__ __forceinline__ bool grid_barrier_partial(GridBarrier* bar, unsigned 
         ok = 0;
         break;
       }
-      __nanosleep(arrive ? 32 : 256);
+      __nanosleep(arrive ? 32 : 2048);
     }
     if (!ok) atomicCAS(status, 0, (int)BFS_ERR_TIMEOUT);
     s_ok = ok;
