@@ -2,6 +2,8 @@
 every forced variant, selectors, statistics, edge cases and error codes.
 
 All comparisons are bit-exact (integer outputs)."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -264,3 +266,35 @@ def test_autotune_keeps_results_and_caches(tmp_path):
     bfs.bfs_sync(g2)
     for i, s in enumerate(roots):
         assert_same(oracle.bfs(og, int(s)), (level[i].cpu().numpy(), parent[i].cpu().numpy()))
+
+
+@pytest.mark.parametrize("narrow_edges", [-1, 1 << 30])
+def test_narrow_levels_never_and_always(narrow_edges):
+    """The narrow_edges knob decides which levels run on half the CTAs: never (-1) and
+    every level (1 << 30), with every variant and the learned selector, on R-MAT and on a
+    grid, bit for bit against the oracle; a default run on the same graph follows."""
+    wpath = os.path.join(os.path.dirname(bfs.__file__), "selector_weights.bin")
+    bfs.bfs_selector_load(wpath)
+    try:
+        for el, roots in ((inputs.rmat(15, 16, seed=81), None), (inputs.grid3d(24), [0])):
+            if roots is None:
+                roots = [int(r) for r in inputs.roots(el, 3, 181)]
+            og = oracle.csr_of(el)
+            g = device_graph_from_edges(el)
+            bfs.bfs_set_tuning(g, narrow_edges=narrow_edges)
+            refs = oracle.bfs_many(og, roots)
+            opts = [bfs.RunOptions(selector=bfs.BFS_SELECT_FORCED, forced_variant=v)
+                    for v in range(bfs.BFS_NUM_VARIANTS)]
+            opts += [bfs.RunOptions(), bfs.RunOptions(selector=bfs.BFS_SELECT_LEARNED)]
+            for s, ref in zip(roots, refs):
+                for o in opts:
+                    parent, level = bfs.run(g, s, o)
+                    bfs.bfs_sync(g)
+                    assert_same(ref, (level.cpu().numpy(), parent.cpu().numpy()), f"narrow {narrow_edges} root {s}")
+            bfs.bfs_set_tuning(g, narrow_edges=0)
+            parent, level = bfs.run(g, roots[0])
+            bfs.bfs_sync(g)
+            assert_same(refs[0], (level.cpu().numpy(), parent.cpu().numpy()), "default after narrow runs")
+            g.destroy()
+    finally:
+        bfs.bfs_selector_set_params(None)
