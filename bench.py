@@ -354,6 +354,52 @@ def batched_config_comparison(bfs, stream):
             "plain_gteps": round(sum(edges) / (plain_ms / 1e3) / 1e9, 3)}
 
 
+def ragged_comparison(bfs, stream):
+    """32 independent R-MAT graphs (scales U{12..20}, one root each) traversed in one launch
+    over their union (bfs_run_ragged) against 32 separate traversals of the same graphs."""
+    import torch
+
+    graphs, rts = inputs.ragged_rmat(32, 5)
+    parts = [bfs.bfs_graph_create_from_edges(torch.from_numpy(el.src).cuda(), torch.from_numpy(el.dst).cuda(), el.n)
+             for el in graphs]
+    u = bfs.bfs_graph_union(parts)
+    levels = [torch.empty(el.n, dtype=torch.int32, device="cuda") for el in graphs]
+    parents = [torch.empty(el.n, dtype=torch.int32, device="cuda") for el in graphs]
+    edges = 0
+    for gp, s, lv, pa in zip(parts, rts, levels, parents):
+        o = bfs.RunOptions(want_counts=True)
+        bfs.bfs_run(gp, s, pa, lv, o)
+        edges += o.edges
+
+    def union_run():
+        bfs.bfs_run_ragged(u, rts, parents, levels)
+
+    def separate_runs():
+        for gp, s, lv, pa in zip(parts, rts, levels, parents):
+            bfs.bfs_run(gp, s, pa, lv)
+
+    out = {}
+    for name, fn in (("one_launch", union_run), ("separate", separate_runs)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = event_pair()
+        e0.record(stream)
+        for _ in range(5):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out[f"{name}_ms"] = round(ms, 3)
+        out[f"{name}_gteps"] = round(edges / (ms / 1e3) / 1e9, 3)
+    bfs.bfs_sync(u)
+    u.destroy()
+    for gp in parts:
+        gp.destroy()
+    out["teps_edges"] = int(edges)
+    return out
+
+
 # ---------------- the GPU arm ----------------
 
 def run_gpu(args, wl):
@@ -565,6 +611,8 @@ def run_gpu(args, wl):
         # one batched traversal against 64 single-root traversals of the same roots
         if wl["kind"] == "rmat" and wl["scale"] != 24 and not args.no_batched_config:
             comp["batched_rmat24"] = batched_config_comparison(bfs, stream)
+        if wl["kind"] == "rmat" and not args.no_batched_config:
+            comp["ragged_32_graphs"] = ragged_comparison(bfs, stream)
         result["comparisons"] = comp
 
     g.destroy()

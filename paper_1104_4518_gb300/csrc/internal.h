@@ -48,7 +48,7 @@ struct __align__(64) LevelCtr {
   unsigned int chunks;            // chunk items of high-degree frontier vertices
   unsigned long long edges;       // degree sum of the frontier
   unsigned long long bins[3];     // degree <= 32, <= 1024, larger
-  unsigned long long pad;
+  unsigned long long pad;          // the level's cursor of dynamically handed-out pull chunks / chunk items
 };
 
 // Edges per chunk item of a high-degree top-down vertex (one CTA pass).

@@ -216,3 +216,13 @@ def workload_rmat(scale: int, n_roots: int, graph_seed: int, root_seed: int, edg
     """R-MAT graph (A,B,C,D = .57,.19,.19,.05, relabelled) plus its seeded roots."""
     g = rmat(scale, edgefactor, seed=graph_seed)
     return g, roots(g, n_roots, root_seed)
+
+
+def ragged_rmat(count: int = 32, seed: int = 5):
+    """`count` R-MAT graphs (edgefactor 16) with scales drawn uniformly from 12..20, one
+    seeded root each: the ragged batch of independent graphs."""
+    rng = np.random.default_rng(seed)
+    scales = rng.integers(12, 21, count)
+    graphs = [rmat(int(sc), 16, seed=1000 * seed + i) for i, sc in enumerate(scales)]
+    rts = [int(roots(g, 1, 7 + i)[0]) for i, g in enumerate(graphs)]
+    return graphs, rts

@@ -84,11 +84,7 @@ def test_batch_host_outputs():
 
 def ragged_workload(count=32, seed=5):
     """`count` R-MAT graphs with scales drawn uniformly from 12..20, one root each."""
-    rng = np.random.default_rng(seed)
-    scales = rng.integers(12, 21, count)
-    graphs = [inputs.rmat(int(sc), 16, seed=1000 * seed + i) for i, sc in enumerate(scales)]
-    roots = [int(inputs.roots(g, 1, 7 + i)[0]) for i, g in enumerate(graphs)]
-    return graphs, roots
+    return inputs.ragged_rmat(count, seed)
 
 
 def test_ragged_32_graphs():
