@@ -394,7 +394,23 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
       }
       // other rows: 32 vertices per warp; the owner lane updates V and F_{k+1}
       const long long nw = ((long long)p.n + 31) / 32;
-      for (long long ww = gwarp; ww < nw; ww += gwarps) {
+      // groups of kGroupWords words: each warp's first group statically, later ones from the
+      // level's cursor (fetched one group ahead).  Full row scans make some groups far
+      // dearer than others; with a static deal the level waited on its slowest warps
+      // (64 roots at R-MAT scale 26: 104.8 ms static, 93.7 ms dynamic).  One fetch per
+      // 16 words keeps the cursor's atomics at about 130 K per level at scale 26.
+      constexpr long long kGroupWords = 16;
+      const long long ngroups = (nw + kGroupWords - 1) / kGroupWords;
+      unsigned long long* cursor = &p.ctr[k % kCtrRing].pad;
+      long long grp = gwarp, next = 0;
+      if (lane == 0) next = gwarps + (long long)atomicAdd(cursor, 1ull);
+      for (long long ww = grp * kGroupWords; grp < ngroups;) {
+        if (ww >= min(nw, (grp + 1) * kGroupWords)) {
+          grp = __shfl_sync(kFull, next, 0);
+          if (grp < ngroups && lane == 0) next = gwarps + (long long)atomicAdd(cursor, 1ull);
+          ww = grp * kGroupWords;
+          continue;
+        }
         const long long v0 = ww * 32 + lane;
         const int v = (int)v0;
         uint64_t need = 0, vv = 0, fv = 0;
@@ -422,6 +438,7 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
           }
         }
         warp_enqueue(p, knext, wq, nbuf, found != 0, v, lane, false);
+        ++ww;
       }
       warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
     }
