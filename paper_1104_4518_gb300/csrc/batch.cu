@@ -35,6 +35,7 @@
 // the number of roots it carries, so fewer, wider traversals win even when
 // the frontier array no longer fits in L2 (measured at scales 22 to 26).
 #include <cooperative_groups.h>
+#include <climits>
 
 #include "claims.cuh"
 #include "device_common.cuh"
@@ -393,25 +394,20 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
         pull_chunk(p, Fc, Fn, knext, v, rb, re, need, lane, cl, wq, nbuf);
       }
       // other rows: 32 vertices per warp; the owner lane updates V and F_{k+1}
-      const long long nw = ((long long)p.n + 31) / 32;
-      // groups of kGroupWords words: each warp's first group statically, later ones from the
-      // level's cursor (fetched one group ahead).  Full row scans make some groups far
-      // dearer than others; with a static deal the level waited on its slowest warps
-      // (64 roots at R-MAT scale 26: 104.8 ms static, 93.7 ms dynamic).  One fetch per
-      // 16 words keeps the cursor's atomics at about 130 K per level at scale 26.
-      constexpr long long kGroupWords = 16;
-      const long long ngroups = (nw + kGroupWords - 1) / kGroupWords;
-      unsigned long long* cursor = &p.ctr[k % kCtrRing].pad;
-      long long grp = gwarp, next = 0;
-      if (lane == 0) next = gwarps + (long long)atomicAdd(cursor, 1ull);
-      for (long long ww = grp * kGroupWords; grp < ngroups;) {
-        if (ww >= min(nw, (grp + 1) * kGroupWords)) {
-          grp = __shfl_sync(kFull, next, 0);
-          if (grp < ngroups && lane == 0) next = gwarps + (long long)atomicAdd(cursor, 1ull);
-          ww = grp * kGroupWords;
-          continue;
-        }
-        const long long v0 = ww * 32 + lane;
+      // word indices fit 32 bits: n < 2^31
+      const int nw = (int)(((long long)p.n + 31) / 32), gw = (int)gwarps;
+      constexpr int kGroupWords = 16;
+      // words [0, S) are dealt one at a time round robin (warp i takes i, i + gw, ...),
+      // the rest in groups of kGroupWords words from the level's cursor, each fetch issued
+      // one group ahead.  Full row scans make some words far dearer than others: with an
+      // all-static deal a level waited on its slowest warps (64 roots at R-MAT scale 26:
+      // 104.6 ms, 94.4 with the dynamic tail).  With few words per warp all are dealt
+      // round robin: 16-word groups from the first word left warps idle on the 2^27-edge
+      // edgefactor-16 and -64 graphs (16 roots: 3 % and 4 % slower).
+      const int S = nw > 64 * gw ? gw * ((nw / 2) / gw) : nw;
+      const int ngroups = (nw - S + kGroupWords - 1) / kGroupWords;
+      auto pull_word = [&](int ww) {
+        const long long v0 = (long long)ww * 32 + lane;
         const int v = (int)v0;
         uint64_t need = 0, vv = 0, fv = 0;
         long long b = 0, e = 0;
@@ -438,7 +434,16 @@ __global__ void __launch_bounds__(kBBlock, 2) batch_kernel(BatchParams p) {
           }
         }
         warp_enqueue(p, knext, wq, nbuf, found != 0, v, lane, false);
-        ++ww;
+      };
+      for (int ww = (int)gwarp; ww < S; ww += gw) pull_word(ww);
+      if (ngroups > 0) {
+        unsigned next = 0;
+        if (lane == 0) next = (unsigned)atomicAdd(&p.ctr[k % kCtrRing].pad, 1ull);
+        for (int grp = (int)__shfl_sync(kFull, next, 0); grp < ngroups; grp = (int)__shfl_sync(kFull, next, 0)) {
+          if (lane == 0) next = (unsigned)atomicAdd(&p.ctr[k % kCtrRing].pad, 1ull);  // fetched one group ahead
+          const int w0 = S + grp * kGroupWords, w1 = min(nw, w0 + kGroupWords);
+          for (int ww = w0; ww < w1; ++ww) pull_word(ww);
+        }
       }
       warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
     }

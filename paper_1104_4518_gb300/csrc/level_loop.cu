@@ -38,6 +38,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <climits>
 #include <cstdio>
 
 #include "device_common.cuh"
@@ -311,15 +312,8 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
   // chunk items of high-degree frontier vertices: one CTA per item; before each
   // item the CTA makes room in its buffers for the item's claims
   const int64_t* items = p.chunks[k & 1];
-  // items are handed out dynamically after each CTA's first: thread 0 fetches the
-  // next free index from the level's counter slot one item ahead
-  unsigned long long* cursor = &p.ctr[k % kCtrRing].pad;
-  if (tid == 0 && blockIdx.x < nchunks) sm.next_item = G + atomicAdd(cursor, 1ull);
-  for (unsigned long long ci = blockIdx.x; ci < nchunks;) {
+  for (unsigned ci = blockIdx.x; ci < nchunks; ci += G) {
     flush_claims_if_full(p, k + 1, sm.cl, kChunkEdges, kBigBuf / 2);
-    const unsigned long long next = sm.next_item;
-    __syncthreads();  // every thread has read the next index before thread 0 replaces it
-    if (tid == 0 && next < nchunks) sm.next_item = G + atomicAdd(cursor, 1ull);
     const int64_t it = items[ci];
     const int v = (int)(it >> 32);
     const long long c = it & 0xffffffffll;
@@ -327,7 +321,6 @@ __device__ void topdown_phase(const LoopParams& p, int k, int variant, unsigned 
     const long long b = rb + c * kChunkEdges;
     const long long e = min(b + (long long)kChunkEdges, re);
     for (long long j = b + tid; j < e; j += kBlock) td_visit(p, cur, nxt, k, v, __ldg(&p.adj[j]), acc, sm.cl);
-    ci = next;
   }
 
   // frontier entry i goes to CTA i % G, so that small frontiers spread over the SMs
@@ -529,11 +522,13 @@ __device__ __forceinline__ void pull_claim(const LoopParams& p, int knext, int v
 // row however sparse the live vertices are (in the last pull levels of a
 // scale-26 R-MAT graph most words hold one live vertex).  Each word's hits are
 // gathered in shared memory and its owner lane writes the word's `nxt` and
-// `vis` (no global atomics on the bitmaps).  Chunks are handed out
-// dynamically, since rows without a frontier neighbour near their top make
-// some chunks far dearer than others: with a static deal the level waited on
-// its slowest warps (R-MAT scale 26: 126.4 ms for the 64 bench roots, 122.3
-// with the dynamic one).
+// `vis` (no global atomics on the bitmaps).  Rows without a frontier
+// neighbour near their top make some chunks far dearer than others, so the
+// second half of a large level's chunks is handed out dynamically: with an
+// all-static deal the level waited on its slowest warps (R-MAT scale 26: 126.4
+// ms for the 64 bench roots, 121.8 with the dynamic tail), and with an
+// all-dynamic one the cursor's atomics, all at once at the start of every
+// level, made the 2^27-edge edgefactor-16 and -64 graphs 11 % and 15 % slower.
 __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc, unsigned G) {
   const uint32_t* cur = p.bits[k % 3];
   uint32_t* nxt = p.bits[(k + 1) % 3];
@@ -544,15 +539,16 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc, unsig
   int* wq = sm.cl.wq[wid];
   uint32_t* hitw = sm.pull_hits[wid];
   int nbuf = 0;
-  const long long nchunks = ((long long)p.nwords + 31) / 32;
-  // chunks are handed out dynamically: each warp's first chunk statically, later ones
-  // from the level's counter slot (the next index is fetched while a chunk is processed)
-  unsigned long long* cursor = &p.ctr[k % kCtrRing].pad;
-  long long c = (long long)wid * G + blockIdx.x;
-  long long next = 0;
-  if (lane == 0) next = gwarps + (long long)atomicAdd(cursor, 1ull);
-  for (; c < nchunks;) {
-    const long long w = c * 32 + lane;
+  // chunk indices fit 32 bits: nwords < 2^26
+  const int nchunks = (p.nwords + 31) / 32, gw = (int)gwarps;
+  // Chunks [0, S) are dealt statically (warp i takes i, i + gw, ...), the
+  // rest from the level's cursor, each fetch issued one chunk ahead.  With
+  // fewer than two chunks per warp the level is all static (S past every chunk).
+  const int S = nchunks > 2 * gw ? gw * max(1, (nchunks / 2) / gw) : INT_MAX;
+  for (int c = wid * (int)G + (int)blockIdx.x; c < nchunks;) {
+    unsigned taken = 0;
+    if (c + gw >= S && lane == 0) taken = (unsigned)atomicAdd(&p.ctr[k % kCtrRing].pad, 1ull);  // used after the chunk
+    const int w = c * 32 + lane;
     const bool has = w < p.nwords;
     const uint32_t vw = has ? p.vis[w] : 0xffffffffu;
     const uint32_t cw = has ? cur[w] : 0u;
@@ -590,8 +586,7 @@ __device__ void pull_phase(const LoopParams& p, int k, Smem& sm, Acc& acc, unsig
       if ((visw | hits) != vw) p.vis[w] = visw | hits;
     }
     __syncwarp();
-    c = __shfl_sync(kFull, next, 0);
-    if (c < nchunks && lane == 0) next = gwarps + (long long)atomicAdd(cursor, 1ull);
+    c = c + gw >= S ? S + (int)__shfl_sync(kFull, taken, 0) : c + gw;
   }
   warp_enqueue(p, knext, wq, nbuf, false, 0, lane, true);
 }

@@ -150,7 +150,7 @@ def test_trained_selector_gain():
     3D grid (80^3, corner root).
 
     Against the method without a selector (one expansion variant at every
-    level, the best of the four for that graph) the learned schedule must be
+    level, the best single variant for that graph) the learned schedule must be
     faster on R-MAT.  On the grid every level is top-down and a level takes
     about 8 us, of which the network's evaluation inside the traversal
     (about 1 us) is a visible share, so there it must stay within 20 % of the
