@@ -597,16 +597,18 @@ def run_gpu(args, wl):
             "tiled_gteps": round(harmonic_gteps(e_one[:len(few)], list(tt.flatten() / 1e3)), 3),
             "how": "the heuristic's per-level schedule (degree-binned / warp top-down levels, dense-frontier "
                    "levels) replayed with the dense-frontier levels on the 2D DCSC tiles"}
-        # autotuned: tuning picked on 8 other seeded roots, then all timed roots
-        if wl["kind"] == "rmat":
-            tune_roots = inputs.roots(el, 8, wl["root_seed"] + 7777)
-            tuned = bfs.bfs_autotune(g, tune_roots)
-            at = timed_roots(lambda s: bfs.bfs_run(g, s, parent, level), large_roots, 1, 1, stream)
-            comp["autotuned_gteps"] = round(harmonic_gteps(e_one, list(at.flatten() / 1e3)), 3)
-            comp["autotuned"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuned.as_dict().items()}
-            bfs.bfs_set_tuning(g, **{f: 0 for f in ("warp_degree", "cta_degree", "pull_thread_degree",
-                                                     "chunk_degree", "batch_topdown_limit", "small_frontier",
-                                                     "batch_width", "narrow_edges")}, alpha=0.0, beta=0.0)
+        # autotuned: tuning picked on 8 other seeded roots (a grid: on the opposite corner, which
+        # its symmetry makes an equivalent root), then all timed roots (a grid's one root: every step)
+        tune_roots = inputs.roots(el, 8, wl["root_seed"] + 7777) if wl["kind"] == "rmat" else [n - 1]
+        tuned = bfs.bfs_autotune(g, tune_roots)
+        at_steps = 1 if wl["kind"] == "rmat" else args.steps
+        at = timed_roots(lambda s: bfs.bfs_run(g, s, parent, level), large_roots, at_steps, 1, stream)
+        comp["autotuned_gteps"] = round(harmonic_gteps(e_one * at_steps, list(at.flatten() / 1e3)), 3)
+        comp["autotuned_ms_per_step"] = round(float(at.sum(axis=1).mean()), 3)
+        comp["autotuned"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuned.as_dict().items()}
+        bfs.bfs_set_tuning(g, **{f: 0 for f in ("warp_degree", "cta_degree", "pull_thread_degree",
+                                                 "chunk_degree", "batch_topdown_limit", "small_frontier",
+                                                 "batch_width", "narrow_edges", "ctas_per_sm")}, alpha=0.0, beta=0.0)
         # the batched configuration's own graph (R-MAT scale 24, graph seed 4 / roots 104): 64 roots in
         # one batched traversal against 64 single-root traversals of the same roots
         if wl["kind"] == "rmat" and wl["scale"] != 24 and not args.no_batched_config:

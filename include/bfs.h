@@ -129,6 +129,11 @@ typedef struct bfs_tuning {
   int32_t narrow_edges;  /* a level whose frontier has at most this many edges runs on half the CTAs of the
                             traversal's grid, which also halves its barrier's arrivals (0 = default 16384;
                             negative = never) */
+  int32_t ctas_per_sm;   /* single-root traversals: CTAs per SM in the persistent grid (0 = default: as many as
+                            fit, two; 1 = one; larger values act as the default).  One CTA per SM halves
+                            every barrier's arrivals and suits graphs of many small levels (3D grid 128^3:
+                            14 % faster) but leaves half the warps of a large level's latency hiding unused
+                            (R-MAT scale 26: 40 % slower) */
 } bfs_tuning;
 
 /* Options of one run (NULL = heuristic selector, no statistics). */
@@ -335,9 +340,10 @@ BFS_API int bfs_get_tuning(const bfs_graph* g, bfs_tuning* t);
 /*
  * Times bfs_run over `nroots` host roots (ids) for a small grid of tuning
  * candidates (bin degrees, pull thread degree, chunk degree, heuristic alpha,
- * beta, small_frontier and narrow_edges; coordinate descent, two sweeps), then
- * bfs_run_batch over the first 64 of them for the batched top-down limit; keeps
- * the fastest as the graph's tuning and copies it to *best.
+ * beta, small_frontier, narrow_edges and ctas_per_sm; coordinate descent, two
+ * sweeps), then bfs_run_batch over the first 64 of them for the batched
+ * top-down limit; keeps the fastest as the graph's tuning and copies it to
+ * *best.
  * Synchronises the stream; results never change, only speed.
  */
 BFS_API int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning* best, void* stream);

@@ -76,7 +76,8 @@ class bfs_tuning(ctypes.Structure):
                 ("pull_thread_degree", ctypes.c_int32), ("chunk_degree", ctypes.c_int32),
                 ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
                 ("batch_topdown_limit", ctypes.c_int32), ("small_frontier", ctypes.c_int32),
-                ("batch_width", ctypes.c_int32), ("narrow_edges", ctypes.c_int32)]
+                ("batch_width", ctypes.c_int32), ("narrow_edges", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -84,6 +84,7 @@ bfs_tuning effective_tuning(const bfs_graph* g) {
   if (!(t.beta > 0.0f)) t.beta = 24.0f;
   if (t.batch_topdown_limit <= 0) t.batch_topdown_limit = std::max(1024, g->n / 64);
   if (t.batch_width != 8 && t.batch_width != 16 && t.batch_width != 32 && t.batch_width != 64) t.batch_width = 64;
+  if (t.ctas_per_sm < 0 || t.ctas_per_sm > 1) t.ctas_per_sm = 0;  // 0: as many as fit
   return t;
 }
 
@@ -911,8 +912,9 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
     const float be[] = {8.0f, 16.0f, 24.0f, 48.0f, 96.0f};
     const int sf[] = {-1, 0, 2 * 4864, 4 * 4864};
     const int ne[] = {-1, 4096, 16384, 65536};
-    for (int knob = 0; knob < 8 && !rc; ++knob) {
-      const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 3 : knob >= 6 ? 4 : 5;
+    const int cs[] = {0, 1};
+    for (int knob = 0; knob < 9 && !rc; ++knob) {
+      const int cnt = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 3 : knob == 8 ? 2 : knob >= 6 ? 4 : 5;
       for (int c = 0; c < cnt && !rc; ++c) {
         bfs_tuning t = cur;
         switch (knob) {
@@ -923,7 +925,8 @@ int bfs_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, bfs_tuning*
           case 4: t.alpha = al[c]; break;
           case 5: t.beta = be[c]; break;
           case 6: t.small_frontier = sf[c]; break;
-          default: t.narrow_edges = ne[c]; break;
+          case 7: t.narrow_edges = ne[c]; break;
+          default: t.ctas_per_sm = cs[c]; break;
         }
         float ms = 0.0f;
         rc = time_plain(t, &ms);

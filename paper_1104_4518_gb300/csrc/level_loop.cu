@@ -1116,7 +1116,7 @@ int launch_level_loop(const RunRequest& r, cudaStream_t s) {
   int per_sm = 0;
   BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, dyn_smem));
   if (per_sm < 1) return fail(BFS_ERR_CUDA, "level loop kernel cannot be resident");
-  const int grid = per_sm * di.sm_count;
+  const int grid = (t.ctas_per_sm > 0 ? std::min(per_sm, t.ctas_per_sm) : per_sm) * di.sm_count;
   if (int e = prepare_barrier(w, 0, grid, s, &p.bar)) return e;
   p.small_frontier = t.small_frontier > 0 ? t.small_frontier : (t.small_frontier == 0 ? (long long)grid * kWarps : 0);
   p.narrow_edges = t.narrow_edges > 0 ? t.narrow_edges : (t.narrow_edges == 0 ? (1ll << 14) : -1);

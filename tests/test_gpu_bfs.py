@@ -268,11 +268,13 @@ def test_autotune_keeps_results_and_caches(tmp_path):
         assert_same(oracle.bfs(og, int(s)), (level[i].cpu().numpy(), parent[i].cpu().numpy()))
 
 
-@pytest.mark.parametrize("narrow_edges", [-1, 1 << 30])
-def test_narrow_levels_never_and_always(narrow_edges):
-    """The narrow_edges knob decides which levels run on half the CTAs: never (-1) and
-    every level (1 << 30), with every variant and the learned selector, on R-MAT and on a
-    grid, bit for bit against the oracle; a default run on the same graph follows."""
+@pytest.mark.parametrize("narrow_edges,ctas_per_sm", [(-1, 0), (1 << 30, 0), (0, 1), (1 << 30, 1)])
+def test_narrow_levels_and_grid_sizes(narrow_edges, ctas_per_sm):
+    """The narrow_edges knob decides which levels run on half the CTAs (never: -1; every
+    level: 1 << 30) and ctas_per_sm the persistent grid's size (two CTAs per SM, or one);
+    every variant and the learned selector, on R-MAT and on a grid, give the oracle's
+    results bit for bit; a default run on the same graph follows (the grid size changes
+    back, and with it the barrier's base)."""
     wpath = os.path.join(os.path.dirname(bfs.__file__), "selector_weights.bin")
     bfs.bfs_selector_load(wpath)
     try:
@@ -281,7 +283,7 @@ def test_narrow_levels_never_and_always(narrow_edges):
                 roots = [int(r) for r in inputs.roots(el, 3, 181)]
             og = oracle.csr_of(el)
             g = device_graph_from_edges(el)
-            bfs.bfs_set_tuning(g, narrow_edges=narrow_edges)
+            bfs.bfs_set_tuning(g, narrow_edges=narrow_edges, ctas_per_sm=ctas_per_sm)
             refs = oracle.bfs_many(og, roots)
             opts = [bfs.RunOptions(selector=bfs.BFS_SELECT_FORCED, forced_variant=v)
                     for v in range(bfs.BFS_NUM_VARIANTS)]
@@ -290,8 +292,9 @@ def test_narrow_levels_never_and_always(narrow_edges):
                 for o in opts:
                     parent, level = bfs.run(g, s, o)
                     bfs.bfs_sync(g)
-                    assert_same(ref, (level.cpu().numpy(), parent.cpu().numpy()), f"narrow {narrow_edges} root {s}")
-            bfs.bfs_set_tuning(g, narrow_edges=0)
+                    assert_same(ref, (level.cpu().numpy(), parent.cpu().numpy()),
+                                f"narrow {narrow_edges}, {ctas_per_sm} CTAs per SM, root {s}")
+            bfs.bfs_set_tuning(g, narrow_edges=0, ctas_per_sm=0)
             parent, level = bfs.run(g, roots[0])
             bfs.bfs_sync(g)
             assert_same(refs[0], (level.cpu().numpy(), parent.cpu().numpy()), "default after narrow runs")
