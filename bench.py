@@ -597,6 +597,17 @@ def run_gpu(args, wl):
             "tiled_gteps": round(harmonic_gteps(e_one[:len(few)], list(tt.flatten() / 1e3)), 3),
             "how": "the heuristic's per-level schedule (degree-binned / warp top-down levels, dense-frontier "
                    "levels) replayed with the dense-frontier levels on the 2D DCSC tiles"}
+        # Sec. 4.2's sorted-output SpMSV: a BFS of expand-sort-compress steps, 2 roots
+        try:
+            srt = timed_roots(lambda s: bfs.bfs_run_sorted(g, s, parent, level, stream), large_roots[:2], 1, 1,
+                              stream)
+            comp["sorted_spmsv_bfs_2_roots"] = {
+                "gteps": round(harmonic_gteps(e_one[:2], list(srt.flatten() / 1e3)), 3),
+                "ms_per_root": round(float(srt.mean()), 3),
+                "how": "bfs_run_sorted: every level one SpMSV with sorted output (the frontier's column entries "
+                       "as 64-bit keys, radix-sorted, the last key of each row kept), a host loop over levels"}
+        except bfs.BfsError as e:  # the keys of a level need about 28 bytes per frontier edge
+            comp["sorted_spmsv_bfs_2_roots"] = {"error": str(e)}
         # autotuned: tuning picked on 8 other seeded roots (a grid: on the opposite corner, which
         # its symmetry makes an equivalent root), then all timed roots (a grid's one root: every step)
         tune_roots = inputs.roots(el, 8, wl["root_seed"] + 7777) if wl["kind"] == "rmat" else [n - 1]

@@ -328,6 +328,39 @@ typedef struct bfs_tile_info {
 } bfs_tile_info;
 BFS_API int bfs_graph_tiles(bfs_graph* g, int32_t rb_bits, int32_t cb_bits, bfs_tile_info* info, void* stream);
 
+/*
+ * One SpMSV step with sorted output (Sec. 4.2, the multiway-merge way of
+ * forming the union of the columns A(:, u) that the frontier selects):
+ * t = A (x) f over the (select2nd, max) semiring of Sec. 3.2, masked by
+ * not(visited) (Algorithm 3's t <- t (.) not(pi)), with every frontier value
+ * the vertex's own id, so t(v) is the largest frontier vertex u with an arc
+ * u -> v (an edge when undirected).  The merge is a stable radix sort of one
+ * 64-bit key per selected entry; t comes out with ascending indices.
+ *   frontier: device int32[nf] vertex ids (any order; repeats allowed);
+ *   visited:  device bitmap uint32[ceil(n / 32)], bit v of word v / 32 set =
+ *             v excluded from t; NULL = no mask;
+ *   out_idx, out_val: device int32 arrays of capacity n (t's indices,
+ *             ascending, and their values);
+ *   *out_count (host): the number of entries of t.
+ * Allocates temporary device memory of about 28 bytes per selected entry and
+ * synchronises the stream.  Errors: BFS_ERR_INVALID_ARG (NULL pointers,
+ * nf < 0, a frontier id outside [0, n)); BFS_ERR_INVALID_GRAPH (an adjacency
+ * id outside [0, n)); BFS_ERR_OOM; BFS_ERR_CUDA.
+ */
+BFS_API int bfs_spmsv_sorted(bfs_graph* g, const int32_t* frontier, int32_t nf, const uint32_t* visited,
+                             int32_t* out_idx, int32_t* out_val, int32_t* out_count, void* stream);
+
+/*
+ * Algorithm 3 with a single process, every level one bfs_spmsv_sorted step:
+ * f <- {s}; while f is not empty: t <- A (x) f masked by not(pi); pi <- pi + t;
+ * f <- t (in ascending id order).  Levels and parents are those of bfs_run;
+ * the traversal takes a few kernels and a host read of t's size per level, so
+ * it is a reference form of the sorted-output SpMSV, far slower than bfs_run.
+ * parent_out, level_out: device int32[n].  Synchronises the stream.  Errors as
+ * bfs_spmsv_sorted, and BFS_ERR_INVALID_ARG for a source outside [0, n).
+ */
+BFS_API int bfs_run_sorted(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_out, void* stream);
+
 /* Waits for the stream (and for the copies of asynchronous host outputs of
  * runs on it) and returns (and clears) the device status of the last run
  * enqueued on it for graph g. */

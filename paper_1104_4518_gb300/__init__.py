@@ -119,6 +119,8 @@ def _declare(lib):
         "bfs_sync": [vp, vp],
         "bfs_run_static": [vp, vp, i32, i64, i32, vp, vp, vp],
         "bfs_graph_tiles": [vp, i32, i32, ctypes.POINTER(bfs_tile_info), vp],
+        "bfs_spmsv_sorted": [vp, vp, i32, vp, vp, vp, ctypes.POINTER(i32), vp],
+        "bfs_run_sorted": [vp, i32, vp, vp, vp],
         "bfs_set_tuning": [vp, ctypes.POINTER(bfs_tuning)],
         "bfs_get_tuning": [vp, ctypes.POINTER(bfs_tuning)],
         "bfs_autotune": [vp, ctypes.POINTER(i32), i32, ctypes.POINTER(bfs_tuning), vp],
@@ -315,6 +317,49 @@ def bfs_graph_tiles(g: Graph, rb_bits: int = 0, cb_bits: int = 0, stream=None, h
         out["cp"] = _device_copy_to_host(info.cp, nzc, "<i4", np.uint32)
         out["ir"] = _device_copy_to_host(info.ir, nnz, "<i2", np.uint16)
     return out
+
+
+def _device_ptr(a, dtype_name: str, what: str) -> int:
+    p, host = _ptr_and_host(a, dtype_name)
+    if host:
+        raise ValueError(f"{what} must be device memory")
+    return p
+
+
+def bfs_spmsv_sorted(g: Graph, frontier, out_idx, out_val, visited=None, stream=None) -> int:
+    """One masked SpMSV step with sorted output (device tensors); returns the entry count.
+
+    visited: an int32 device tensor holding the uint32 bitmap words, or None (no mask)."""
+    nf = int(frontier.shape[0])
+    pf = _device_ptr(frontier, "int32", "frontier")
+    pv = 0 if visited is None else _device_ptr(visited, "int32", "visited")
+    cnt = ctypes.c_int32()
+    _check(lib().bfs_spmsv_sorted(g.handle, pf, nf, pv or None, _device_ptr(out_idx, "int32", "out_idx"),
+                                  _device_ptr(out_val, "int32", "out_val"), ctypes.byref(cnt), _stream_handle(stream)))
+    return cnt.value
+
+
+def spmsv_sorted(g: Graph, frontier, visited=None, stream=None):
+    """t = A (x) f masked by not(visited), as (indices ascending, values) device tensors."""
+    torch = _torch()
+    idx = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    val = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    cnt = bfs_spmsv_sorted(g, frontier, idx, val, visited, stream)
+    return idx[:cnt], val[:cnt]
+
+
+def bfs_run_sorted(g: Graph, source: int, parent_out, level_out, stream=None):
+    """BFS of sorted-output SpMSV steps (device outputs int32[n])."""
+    _check(lib().bfs_run_sorted(g.handle, int(source), _device_ptr(parent_out, "int32", "parent_out"),
+                                _device_ptr(level_out, "int32", "level_out"), _stream_handle(stream)))
+
+
+def run_sorted(g: Graph, source: int, stream=None):
+    torch = _torch()
+    parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    level = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    bfs_run_sorted(g, source, parent, level, stream)
+    return parent, level
 
 
 # ---------------- options ----------------

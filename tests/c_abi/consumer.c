@@ -37,6 +37,12 @@ int main(int argc, char** argv) {
     bfs_tile_info info;
     bad |= check("bfs_graph_tiles without a graph", bfs_graph_tiles(NULL, 0, 0, &info, NULL), BFS_ERR_INVALID_ARG);
   }
+  {
+    int32_t cnt = 0;
+    bad |= check("bfs_spmsv_sorted without a graph", bfs_spmsv_sorted(NULL, buf, 1, NULL, buf, buf, &cnt, NULL),
+                 BFS_ERR_INVALID_ARG);
+    bad |= check("bfs_run_sorted without a graph", bfs_run_sorted(NULL, 0, buf, buf, NULL), BFS_ERR_INVALID_ARG);
+  }
   if (g != NULL) {
     fprintf(stderr, "a failed create left a graph behind\n");
     bad = 1;
