@@ -608,6 +608,20 @@ def run_gpu(args, wl):
                        "as 64-bit keys, radix-sorted, the last key of each row kept), a host loop over levels"}
         except bfs.BfsError as e:  # the keys of a level need about 28 bytes per frontier edge
             comp["sorted_spmsv_bfs_2_roots"] = {"error": str(e)}
+        # symmetric half storage: a BFS that reads only the entries above the diagonal, 2 roots
+        if not wl.get("directed"):
+            try:
+                hinfo = bfs.bfs_graph_half(g, host_copy=False)
+                hrt = timed_roots(lambda s: bfs.bfs_run_half(g, s, parent, level, stream), large_roots[:2], 1, 1,
+                                  stream)
+                comp["half_storage_bfs_2_roots"] = {
+                    "gteps": round(harmonic_gteps(e_one[:2], list(hrt.flatten() / 1e3)), 3),
+                    "ms_per_root": round(float(hrt.mean()), 3),
+                    "adjacency_bytes": 4 * int(hinfo["nnz"]), "full_adjacency_bytes": 4 * int(nnz),
+                    "how": "bfs_run_half: per level a pull over the unvisited half rows (largest frontier "
+                           "neighbour above) and a push from the frontier's half rows (atomicMax from below)"}
+            except bfs.BfsError as e:
+                comp["half_storage_bfs_2_roots"] = {"error": str(e)}
         # autotuned: tuning picked on 8 other seeded roots (a grid: on the opposite corner, which
         # its symmetry makes an equivalent root), then all timed roots (a grid's one root: every step)
         tune_roots = inputs.roots(el, 8, wl["root_seed"] + 7777) if wl["kind"] == "rmat" else [n - 1]

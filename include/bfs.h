@@ -361,6 +361,36 @@ BFS_API int bfs_spmsv_sorted(bfs_graph* g, const int32_t* frontier, int32_t nf, 
  */
 BFS_API int bfs_run_sorted(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_out, void* stream);
 
+/*
+ * Symmetric half storage (the paper's closing note: an undirected graph's
+ * adjacency is symmetric, so one triangle holds it): U keeps, of each row v,
+ * the entries w > v, ascending.  bfs_graph_half builds U on the device the
+ * first time (half the entries of a loop-free symmetric CSR) and keeps it with
+ * g; the pointers stay valid until g is destroyed:
+ *   offsets (int64[n + 1]), adj (int32[nnz]) on the device.
+ * Synchronises the stream.  Errors: BFS_ERR_INVALID_ARG (NULL g or info),
+ * BFS_ERR_UNSUPPORTED (a directed graph), BFS_ERR_OOM, BFS_ERR_CUDA.
+ */
+typedef struct bfs_half_info {
+  int64_t nnz;
+  const int64_t* offsets;
+  const int32_t* adj;
+} bfs_half_info;
+BFS_API int bfs_graph_half(bfs_graph* g, bfs_half_info* info, void* stream);
+
+/*
+ * BFS that reads only U: a level pulls each unvisited v's U row from the top
+ * (the first frontier entry is v's largest frontier neighbour above v, hence
+ * its parent), then pushes each frontier vertex u to the entries of its U row
+ * that are still unreached (atomicMax: the largest neighbour below them).
+ * Levels and parents are those of bfs_run.  A few kernels and a host read per
+ * level; a reference form of half storage, slower than bfs_run.
+ * parent_out, level_out: device int32[n].  Builds U if g has none;
+ * synchronises the stream.  Errors as bfs_graph_half, and BFS_ERR_INVALID_ARG
+ * for a source outside [0, n) or NULL outputs.
+ */
+BFS_API int bfs_run_half(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_out, void* stream);
+
 /* Waits for the stream (and for the copies of asynchronous host outputs of
  * runs on it) and returns (and clears) the device status of the last run
  * enqueued on it for graph g. */

@@ -90,6 +90,10 @@ class bfs_tile_info(ctypes.Structure):
                 ("cp", ctypes.c_void_p), ("ir", ctypes.c_void_p)]
 
 
+class bfs_half_info(ctypes.Structure):
+    _fields_ = [("nnz", ctypes.c_int64), ("offsets", ctypes.c_void_p), ("adj", ctypes.c_void_p)]
+
+
 class bfs_opts(ctypes.Structure):
     _fields_ = [("selector", ctypes.c_int32), ("forced_variant", ctypes.c_int32),
                 ("schedule", ctypes.POINTER(ctypes.c_int32)), ("schedule_len", ctypes.c_int32),
@@ -121,6 +125,8 @@ def _declare(lib):
         "bfs_graph_tiles": [vp, i32, i32, ctypes.POINTER(bfs_tile_info), vp],
         "bfs_spmsv_sorted": [vp, vp, i32, vp, vp, vp, ctypes.POINTER(i32), vp],
         "bfs_run_sorted": [vp, i32, vp, vp, vp],
+        "bfs_graph_half": [vp, ctypes.POINTER(bfs_half_info), vp],
+        "bfs_run_half": [vp, i32, vp, vp, vp],
         "bfs_set_tuning": [vp, ctypes.POINTER(bfs_tuning)],
         "bfs_get_tuning": [vp, ctypes.POINTER(bfs_tuning)],
         "bfs_autotune": [vp, ctypes.POINTER(i32), i32, ctypes.POINTER(bfs_tuning), vp],
@@ -359,6 +365,32 @@ def run_sorted(g: Graph, source: int, stream=None):
     parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
     level = torch.empty(g.n, dtype=torch.int32, device="cuda")
     bfs_run_sorted(g, source, parent, level, stream)
+    return parent, level
+
+
+def bfs_graph_half(g: Graph, stream=None, host_copy: bool = True) -> dict:
+    """The graph's symmetric half storage (row v: its entries above v), built on first use;
+    with host_copy, NumPy copies of offsets (int64[n + 1]) and adj (int32[nnz])."""
+    info = bfs_half_info()
+    _check(lib().bfs_graph_half(g.handle, ctypes.byref(info), _stream_handle(stream)))
+    out = {"nnz": info.nnz}
+    if host_copy:
+        out["offsets"] = _device_copy_to_host(info.offsets, g.n + 1, "<i8", np.int64)
+        out["adj"] = _device_copy_to_host(info.adj, info.nnz, "<i4", np.int32)
+    return out
+
+
+def bfs_run_half(g: Graph, source: int, parent_out, level_out, stream=None):
+    """BFS that reads only the half storage (device outputs int32[n])."""
+    _check(lib().bfs_run_half(g.handle, int(source), _device_ptr(parent_out, "int32", "parent_out"),
+                              _device_ptr(level_out, "int32", "level_out"), _stream_handle(stream)))
+
+
+def run_half(g: Graph, source: int, stream=None):
+    torch = _torch()
+    parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    level = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    bfs_run_half(g, source, parent, level, stream)
     return parent, level
 
 

@@ -241,6 +241,8 @@ static int read_status(Workspace* w, cudaStream_t s) {
   return BFS_OK;
 }
 
+void free_half(const bfs_graph* g);  // half_storage.cu: the graph's half storage, if any
+
 static int check_graph(const bfs_graph* g) {
   if (!g) return fail(BFS_ERR_INVALID_ARG, "NULL graph");
   return BFS_OK;
@@ -530,6 +532,7 @@ void bfs_graph_destroy(bfs_graph* g) {
   if (g->d_dead) cudaFree(g->d_dead);
   if (g->d_big) cudaFree(g->d_big);
   free_tiles(g->tiles);
+  free_half(g);
   delete g;
 }
 

@@ -43,6 +43,11 @@ int main(int argc, char** argv) {
                  BFS_ERR_INVALID_ARG);
     bad |= check("bfs_run_sorted without a graph", bfs_run_sorted(NULL, 0, buf, buf, NULL), BFS_ERR_INVALID_ARG);
   }
+  {
+    bfs_half_info hinfo;
+    bad |= check("bfs_graph_half without a graph", bfs_graph_half(NULL, &hinfo, NULL), BFS_ERR_INVALID_ARG);
+    bad |= check("bfs_run_half without a graph", bfs_run_half(NULL, 0, buf, buf, NULL), BFS_ERR_INVALID_ARG);
+  }
   if (g != NULL) {
     fprintf(stderr, "a failed create left a graph behind\n");
     bad = 1;

@@ -38,6 +38,8 @@ def lib():
         "bfs_level_features": [i32, i64, i32, i64, i64, i64, i64, vp, vp],
         "bfs_spmsv_sorted": [vp, vp, i32, vp, vp, vp, vp, vp],
         "bfs_run_sorted": [vp, i32, vp, vp, vp],
+        "bfs_graph_half": [vp, vp, vp],
+        "bfs_run_half": [vp, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         getattr(lib, name).argtypes = args
@@ -84,6 +86,8 @@ def test_runs_reject_missing_graphs_and_bad_sources(lib):
     cnt = ctypes.c_int32(5)
     expect(lib, lib.bfs_spmsv_sorted(None, p, 1, None, p, p, ctypes.byref(cnt), None), INVALID_ARG, "NULL graph")
     expect(lib, lib.bfs_run_sorted(None, 0, p, p, None), INVALID_ARG, "NULL graph")
+    expect(lib, lib.bfs_graph_half(None, None, None), INVALID_ARG, "NULL graph")
+    expect(lib, lib.bfs_run_half(None, 0, p, p, None), INVALID_ARG, "NULL graph")
 
 
 def test_static_entry_point_checks_before_any_device_work(lib):
