@@ -386,8 +386,9 @@ BFS_API int bfs_graph_half(bfs_graph* g, bfs_half_info* info, void* stream);
  * Levels and parents are those of bfs_run.  A few kernels and a host read per
  * level; a reference form of half storage, slower than bfs_run.
  * parent_out, level_out: device int32[n].  Builds U if g has none;
- * synchronises the stream.  Errors as bfs_graph_half, and BFS_ERR_INVALID_ARG
- * for a source outside [0, n) or NULL outputs.
+ * synchronises the stream.  The graph's ids are taken as valid, as in bfs_run
+ * (BFS_VALIDATE at creation checks them).  Errors as bfs_graph_half, and
+ * BFS_ERR_INVALID_ARG for a source outside [0, n) or NULL outputs.
  */
 BFS_API int bfs_run_half(bfs_graph* g, int32_t source, int32_t* parent_out, int32_t* level_out, void* stream);
 
